@@ -1,0 +1,196 @@
+"""Algorithm 4: projected, preconditioned nonlinear conjugate gradient method
+for micromagnetics, with the beta*ZA restart rule (Sec. 2.2), the descent
+safeguard, a line search that avoids too long steps, and the stopping rules
+t1-t3 (Sec. 3.1).
+
+Steps per field (the order of Algorithm 4):
+  init: x_0 = N(m_0); g_0 = Pi(grad F(x_0)); solve P_0 y_0 = g_0; d_0 = -y_0
+  loop: alpha_j from the line search on F(N(x_j + alpha d_j));
+        x_{j+1} = N(x_j + alpha_j d_j); g_{j+1} = Pi(grad F(x_{j+1}));
+        solve P_{j+1} y_{j+1} = g_{j+1};
+        d_{j+1} = -y_{j+1} + beta*ZA d_j;
+        stop when t1, t2 and t3 all hold.
+
+beta*ZA = (g+ - g).y+ / (g+ - g).d  if y+.g+ > y+.g, else 0.
+
+Readings where the paper is silent or garbled (shared exactly with the CUDA
+path):
+  * Descent safeguard ("replace y by g if g.d > 0", indices garbled): if the
+    new direction has g.d >= 0, y is replaced by g, beta is recomputed with
+    it, and if g.d is still >= 0 the direction becomes d = -g.  The initial
+    direction gets the same treatment.
+  * Line search (defined only by reference to Fischbacher et al. 2017, "which
+    avoids too long steps"): phi(a) = F(N(x + a d)), phi'(a) from Eq. (opt2).
+    Step cap a_max = theta_max / max_i |d_i|.  Trial a_t = min(a_prev, a_max)
+    (a_prev = 1 at the start of each field).  One evaluation at a_t, then the
+    minimiser a_s of the cubic Hermite interpolant of (phi(0), phi'(0),
+    phi(a_t), phi'(a_t)), clamped to [0.1 a_t, min(4 a_t, a_max)] (when the
+    cubic has no minimiser: 4 a_t if phi'(a_t) < 0 else a_t/2, then clamped),
+    and one evaluation at a_s.  The lower of the two (a_s on ties) is taken
+    if it satisfies phi(a) <= phi(0) + c1 a phi'(0); otherwise a halves from
+    min(a_t, a_s)/2 until that holds (at most max_backtrack evaluations).  If
+    nothing qualifies the minimiser stops with status "stalled" and x
+    unchanged.  This gives exactly two evaluations per iteration in the
+    common case, matching evals = 2 nli + n_fields in Tables 1 and 2.
+  * Stopping rules t1-t3 use internal units (fem.Units) and the max norm
+    over all 3N components.
+  * Counters: evals (function evaluations), nli (iterations), li (products
+    with H in the inner solves), mi (products with K_phi in the loop of the
+    Poisson solves; 0 with the direct solver), ls_extra (evaluations spent
+    backtracking).
+
+Pins (tests/test_oracle_ncg.py): the Stoner-Wohlfarth switching field of a
+small particle (exchange-coupled uniform rotation, demag off), the exact
+beta*ZA branches on hand-made vectors, the iteration identities
+evals = 2 nli + 1 and li = j_max (nli + 1) when every inner solve runs to
+j_max, monotone energy decrease, and |m_i| = 1 at every accepted iterate.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .energy import evaluate, normalize, ftilde_derivative
+from .precond import precond_solve
+
+
+@dataclass
+class Params:
+    tau_F: float = 1e-10
+    jmax: int = 4
+    max_iter: int = 10000
+    theta_max: float = 0.1
+    c1: float = 1e-4
+    max_backtrack: int = 10
+    keep_last_term: bool = False
+    poisson: str = "direct"        # "direct" or "cg"
+    poisson_tol: float = 1e-10
+
+
+@dataclass
+class Result:
+    m: np.ndarray
+    F: float
+    terms: dict
+    g: np.ndarray
+    phi: np.ndarray
+    status: str
+    stats: dict = field(default_factory=dict)
+
+
+def beta_za(g_new, g_old, y_new, d_old):
+    """beta*ZA (Hestenes-Stiefel with restart)."""
+    if float(np.sum(y_new * g_new)) > float(np.sum(y_new * g_old)):
+        dg = g_new - g_old
+        den = float(np.sum(dg * d_old))
+        if den == 0.0:
+            return 0.0
+        return float(np.sum(dg * y_new)) / den
+    return 0.0
+
+
+def direction(g_new, g_old, y_new, d_old):
+    """d = -y + beta*ZA d_old with the descent safeguard."""
+    beta = beta_za(g_new, g_old, y_new, d_old)
+    d = -y_new + beta * d_old
+    if float(np.sum(g_new * d)) >= 0.0:
+        beta = beta_za(g_new, g_old, g_new, d_old)
+        d = -g_new + beta * d_old
+        if float(np.sum(g_new * d)) >= 0.0:
+            d = -g_new.copy()
+    return d
+
+
+def cubic_step(f0, g0, a, f1, g1):
+    """Minimiser of the cubic Hermite interpolant through (0, f0, g0) and
+    (a, f1, g1), or None if it has none."""
+    d1 = g0 + g1 - 3.0 * (f1 - f0) / a
+    disc = d1 * d1 - g0 * g1
+    if disc <= 0.0:                  # no stationary point, or only an inflection
+        return None
+    d2 = np.sqrt(disc)
+    den = g1 - g0 + 2.0 * d2
+    if den == 0.0:
+        return None
+    return a - a * (g1 + d2 - d1) / den
+
+
+def minimize(P, m0, h, params=None, phi0=None):
+    """Minimise F at reduced field h starting from m0 (Nm, 3)."""
+    p = params or Params()
+    st = {"evals": 0, "nli": 0, "li": 0, "mi": 0, "ls_extra": 0}
+
+    def ev(m, phi_warm):
+        e = evaluate(P, m, h, p.poisson, phi0=phi_warm, tol=p.poisson_tol)
+        st["evals"] += 1
+        st["mi"] += e["poisson_steps"]
+        return e
+
+    def pre(m, e):
+        y, steps = precond_solve(P, m, e["grad"], e["g"], p.jmax, p.keep_last_term)
+        st["li"] += steps
+        return y
+
+    x = normalize(np.asarray(m0, dtype=np.float64))
+    e = ev(x, phi0)
+    phi = e["phi"]
+    y = pre(x, e)
+    d = -y
+    if float(np.sum(e["g"] * d)) >= 0.0:
+        d = -e["g"].copy()
+    a_prev = 1.0
+    status = "max_iter"
+    if not np.isfinite(e["F"]):
+        status = "nonfinite"
+    elif np.max(np.abs(e["g"])) == 0.0:
+        status = "converged"
+    while status == "max_iter" and st["nli"] < p.max_iter:
+        F0 = e["F"]
+        dphi0 = float(np.sum(e["g"] * d))
+        a_max = p.theta_max / np.max(np.linalg.norm(d, axis=1))
+        a_t = min(a_prev, a_max)
+        u_t = x + a_t * d
+        x_t = normalize(u_t)
+        e_t = ev(x_t, phi)
+        phi = e_t["phi"]
+        dphi_t = ftilde_derivative(e_t["g"], u_t, d)
+        a_s = cubic_step(F0, dphi0, a_t, e_t["F"], dphi_t)
+        if a_s is None or not np.isfinite(a_s):
+            a_s = 4.0 * a_t if dphi_t < 0.0 else 0.5 * a_t
+        a_s = min(max(a_s, 0.1 * a_t), min(4.0 * a_t, a_max))
+        x_s = normalize(x + a_s * d)
+        e_s = ev(x_s, phi)
+        phi = e_s["phi"]
+        if e_s["F"] <= e_t["F"]:
+            a_b, x_b, e_b = a_s, x_s, e_s
+        else:
+            a_b, x_b, e_b = a_t, x_t, e_t
+        if not (e_b["F"] <= F0 + p.c1 * a_b * dphi0):
+            found = False
+            a = 0.5 * min(a_t, a_s)
+            for _ in range(p.max_backtrack):
+                x_k = normalize(x + a * d)
+                e_k = ev(x_k, phi)
+                st["ls_extra"] += 1
+                phi = e_k["phi"]
+                if e_k["F"] <= F0 + p.c1 * a * dphi0:
+                    a_b, x_b, e_b = a, x_k, e_k
+                    found = True
+                    break
+                a *= 0.5
+            if not found:
+                status = "stalled"
+                break
+        st["nli"] += 1
+        if not np.isfinite(e_b["F"]):
+            status = "nonfinite"
+            break
+        t1 = F0 - e_b["F"] < p.tau_F * (1.0 + abs(e_b["F"]))
+        t2 = np.max(np.abs(x - x_b)) < np.sqrt(p.tau_F) * (1.0 + np.max(np.abs(x_b)))
+        t3 = np.max(np.abs(e_b["g"])) < p.tau_F ** (1.0 / 3.0) * (1.0 + abs(e_b["F"]))
+        y_new = pre(x_b, e_b)
+        d = direction(e_b["g"], e["g"], y_new, d)
+        x, e, a_prev = x_b, e_b, a_b
+        if t1 and t2 and t3:
+            status = "converged"
+    return Result(m=x, F=e["F"], terms=e["terms"], g=e["g"], phi=phi,
+                  status=status, stats=st)

@@ -1,0 +1,135 @@
+"""Seeded synthetic workloads shaped like the paper's soft- and hard-magnetic
+test cases (Sec. 3.2-3.4): a permalloy cube, a hard-magnetic Nd2Fe14B cube
+and a polycrystalline cube with a grain-boundary phase, each inside an air
+box for the magnetostatic potential.
+
+A material table has one row per region label: (Ms [A/m], A [J/m],
+K1 [J/m^3], easy-axis x, y, z).  Row 0 is air (Ms = 0).  Fields are applied
+flux densities mu0*H in tesla, one row per field step.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .mesh import Mesh, cube_in_box, jitter_nodes, voronoi_regions
+
+MU0 = 4e-7 * np.pi
+
+PERMALLOY = dict(Ms=8.0e5, A=1.3e-11, K1=0.0)
+ND2FE14B = dict(Ms=1.28e6, A=7.7e-12, K1=4.3e6)
+
+
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    materials: np.ndarray      # (R, 6)
+    fields: np.ndarray         # (F, 3) mu0*H in T
+    m0: np.ndarray             # (N, 3) unit vectors (only magnetic nodes matter)
+    meta: dict = field(default_factory=dict)
+
+
+def random_unit_vectors(n, seed):
+    """n independent unit vectors uniform on the sphere (normalised Gaussians)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def cone_axes(n, max_angle_deg, seed):
+    """n unit vectors uniform within a cone of half-angle max_angle about +z
+    (cos(theta) ~ U[cos max, 1], azimuth ~ U[0, 2 pi))."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(np.cos(np.radians(max_angle_deg)), 1.0, size=n)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    s = np.sqrt(1.0 - c * c)
+    return np.stack([s * np.cos(phi), s * np.sin(phi), c], axis=1)
+
+
+def _material_table(rows):
+    t = np.zeros((len(rows), 6))
+    for r, row in enumerate(rows):
+        t[r] = row
+    return t
+
+
+def small_cube(n_mag=4, h=2.0e-9, box_factor=2.0, Ms=8.0e5, A=1.3e-11, K1=0.0,
+               axis=(0.0, 0.0, 1.0), jitter=0.0, seed=0, m0=None,
+               fields=((0.0, 0.0, 0.0),)):
+    """A small cube magnet in an air box for tests."""
+    mesh = cube_in_box(n_mag, h, box_factor)
+    if jitter > 0:
+        mesh = jitter_nodes(mesh, jitter, seed)
+    ax = np.asarray(axis, dtype=np.float64)
+    ax = ax / np.linalg.norm(ax)
+    mats = _material_table([(0, 0, 0, 0, 0, 1), (Ms, A, K1, *ax)])
+    if m0 is None:
+        m0 = random_unit_vectors(mesh.n_nodes, seed + 1)
+    else:
+        m0 = np.broadcast_to(np.asarray(m0, dtype=np.float64), (mesh.n_nodes, 3)).copy()
+        m0 /= np.linalg.norm(m0, axis=1, keepdims=True)
+    return Workload(name=f"small_cube_{n_mag}", mesh=mesh, materials=mats,
+                    fields=np.asarray(fields, dtype=np.float64).reshape(-1, 3), m0=m0,
+                    meta={"n_mag": n_mag, "h": h, "box_factor": box_factor})
+
+
+def soft_cube(n_mag=16, edge=40e-9, box_factor=2.0, seed=1, n_fields=21):
+    """Permalloy cube (40 nm, Ms 8.0e5 A/m, A 1.3e-11 J/m, K 0) of n_mag^3
+    voxels (6 tets each) in an air box of box_factor x edge with a grounded
+    outer boundary; random initial magnetisation; field along x swept from
+    +100 mT to -100 mT."""
+    h = edge / n_mag
+    mesh = cube_in_box(n_mag, h, box_factor)
+    mats = _material_table([(0, 0, 0, 0, 0, 1),
+                            (PERMALLOY["Ms"], PERMALLOY["A"], PERMALLOY["K1"], 1, 0, 0)])
+    b = np.linspace(0.1, -0.1, n_fields)
+    fields = np.stack([b, np.zeros_like(b), np.zeros_like(b)], axis=1)
+    m0 = random_unit_vectors(mesh.n_nodes, seed)
+    return Workload(name=f"soft_cube_{n_mag}", mesh=mesh, materials=mats, fields=fields,
+                    m0=m0, meta={"edge": edge, "h": h, "seed": seed})
+
+
+def hard_cube(n_mag=48, edge=80e-9, box_factor=2.0, seed=2, n_fields=40,
+              b_stop=-8.0, jitter=0.07, tilt_deg=1.0):
+    """Nd2Fe14B cube (80 nm, Ms 1.28e6 A/m, A 7.7e-12 J/m, K1 4.3e6 J/m^3),
+    easy axis tilted tilt_deg from z towards x, n_mag^3 voxels with jittered
+    interior nodes, air box of box_factor x edge; m0 = +z; field along -z from
+    0 to b_stop tesla in n_fields values."""
+    h = edge / n_mag
+    mesh = cube_in_box(n_mag, h, box_factor)
+    if jitter > 0:
+        mesh = jitter_nodes(mesh, jitter, seed)
+    t = np.radians(tilt_deg)
+    mats = _material_table([(0, 0, 0, 0, 0, 1),
+                            (ND2FE14B["Ms"], ND2FE14B["A"], ND2FE14B["K1"],
+                             np.sin(t), 0.0, np.cos(t))])
+    b = np.linspace(0.0, b_stop, n_fields)
+    fields = np.stack([np.zeros_like(b), np.zeros_like(b), b], axis=1)
+    m0 = np.tile([0.0, 0.0, 1.0], (mesh.n_nodes, 1))
+    return Workload(name=f"hard_cube_{n_mag}", mesh=mesh, materials=mats, fields=fields,
+                    m0=m0, meta={"edge": edge, "h": h, "seed": seed, "jitter": jitter})
+
+
+def polycrystal_cube(n_mag=114, edge=200e-9, box_factor=2.0, n_grains=27, seed=3,
+                     gb_thickness=2e-9, cone_deg=15.0, n_fields=60, b_stop=-8.0,
+                     gb_factor=0.4):
+    """Polycrystalline Nd2Fe14B cube: n_grains Voronoi grains with easy axes
+    uniform in a cone about +z, a grain-boundary phase of thickness
+    gb_thickness whose Ms and K1 are scaled by gb_factor (A unchanged),
+    air box of box_factor x edge; m0 = +z; field along -z."""
+    h = edge / n_mag
+    mesh = cube_in_box(n_mag, h, box_factor)
+    half = edge / 2.0
+    mesh, seeds = voronoi_regions(mesh, n_grains, -half, half, gb_thickness, seed)
+    axes = cone_axes(n_grains, cone_deg, seed + 1000)
+    rows = [(0, 0, 0, 0, 0, 1)]
+    for g in range(n_grains):
+        rows.append((ND2FE14B["Ms"], ND2FE14B["A"], ND2FE14B["K1"], *axes[g]))
+    rows.append((gb_factor * ND2FE14B["Ms"], ND2FE14B["A"], gb_factor * ND2FE14B["K1"], 0, 0, 1))
+    mats = _material_table(rows)
+    b = np.linspace(0.0, b_stop, n_fields)
+    fields = np.stack([np.zeros_like(b), np.zeros_like(b), b], axis=1)
+    m0 = np.tile([0.0, 0.0, 1.0], (mesh.n_nodes, 1))
+    return Workload(name=f"polycrystal_{n_grains}g_{n_mag}", mesh=mesh, materials=mats,
+                    fields=fields, m0=m0,
+                    meta={"edge": edge, "h": h, "seed": seed, "grain_seeds": seeds})

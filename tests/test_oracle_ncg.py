@@ -1,0 +1,148 @@
+"""Pins of Algorithm 4 (projected preconditioned NCG), beta*ZA, the descent
+safeguard, the line search and the field loop."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import fem, energy, ncg, curve
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_iteration_counts.txt")
+
+
+def test_beta_za_branches():
+    g_old = np.array([[1.0, 0.0, 0.0]])
+    g_new = np.array([[0.0, 2.0, 0.0]])
+    d_old = np.array([[-1.0, -1.0, 0.0]])
+    y_new = np.array([[0.0, 1.0, 0.0]])          # y.g_new = 2 > y.g_old = 0
+    # (g+ - g).y+ = 2, (g+ - g).d = 1 - 2 = -1
+    assert ncg.beta_za(g_new, g_old, y_new, d_old) == pytest.approx(-2.0)
+    y_bad = np.array([[1.0, 0.0, 0.0]])          # y.g_new = 0 < y.g_old = 1 -> restart
+    assert ncg.beta_za(g_new, g_old, y_bad, d_old) == 0.0
+    # tie -> restart
+    assert ncg.beta_za(g_new, g_new, y_new, d_old) == 0.0
+
+
+def test_direction_safeguard():
+    g_old = np.array([[1.0, 0.0, 0.0]])
+    g_new = np.array([[0.0, 1.0, 0.0]])
+    d_old = np.array([[0.0, 10.0, 0.0]])
+    # y pointing against g: -y is ascent, beta = 0 -> replaced by y = g
+    y_new = np.array([[0.0, -1.0, 0.0]])
+    d = ncg.direction(g_new, g_old, y_new, d_old)
+    assert float(np.sum(g_new * d)) < 0
+    # a regular case keeps d = -y + beta d_old
+    y_ok = np.array([[0.0, 0.5, 0.0]])
+    d_prev = np.array([[-1.0, 0.0, 0.0]])
+    beta = ncg.beta_za(g_new, g_old, y_ok, d_prev)
+    assert beta == pytest.approx(0.5)
+    np.testing.assert_allclose(ncg.direction(g_new, g_old, y_ok, d_prev), [[-0.5, -0.5, 0.0]])
+
+
+def test_cubic_step_exact_for_cubics():
+    # phi(a) = a^3 - 3a has its local minimum at a = 1
+    assert ncg.cubic_step(0.0, -3.0, 2.0, 2.0, 9.0) == pytest.approx(1.0)
+    # phi(a) = (a - 0.3)^2
+    f = lambda a: (a - 0.3) ** 2
+    df = lambda a: 2 * (a - 0.3)
+    assert ncg.cubic_step(f(0), df(0), 1.0, f(1.0), df(1.0)) == pytest.approx(0.3)
+    # phi(a) = -a^3: no minimiser
+    assert ncg.cubic_step(0.0, 0.0, 1.0, -1.0, -3.0) is None
+
+
+def _sw_problem():
+    t = np.radians(1.0)
+    wl = synth.small_cube(n_mag=2, h=1e-9, Ms=1.28e6, A=7.7e-12, K1=4.3e6,
+                          axis=(np.sin(t), 0.0, np.cos(t)), m0=(0, 0, 1))
+    P = fem.assemble_workload(wl)
+    P.D = sp.csr_matrix(P.D.shape)          # magnetostatics off: pure SW particle
+    bK = 2 * 4.3e6 / 1.28e6
+    hsw = (np.sin(t) ** (2 / 3) + np.cos(t) ** (2 / 3)) ** -1.5
+    return P, bK * hsw
+
+
+@pytest.mark.parametrize("jmax", [0, 4])
+def test_stoner_wohlfarth_switching_field(jmax):
+    """A 2 nm Nd2Fe14B cube (far below the exchange length) rotates
+    coherently; with the field 1 degree off the easy axis it must switch
+    between 0.995 and 1.005 of h_sw = 2K/(mu0 Ms) (cos^2/3 + sin^2/3)^-3/2."""
+    P, bsw = _sw_problem()
+    for f, switched in ((0.995, False), (1.005, True)):
+        m = np.tile([0.0, 0.0, 1.0], (P.n_mag, 1))
+        r = ncg.minimize(P, m, P.units.field_int([0, 0, -f * bsw]), ncg.Params(jmax=jmax))
+        assert r.status == "converged"
+        assert (r.m[:, 2].mean() < 0) == switched
+        assert r.m[:, 2].std() < 1e-5
+
+
+def _soft_problem():
+    wl = synth.small_cube(n_mag=3, h=2e-9, jitter=0.05, seed=9)
+    return wl, fem.assemble_workload(wl)
+
+
+def test_iteration_identities_and_invariants():
+    wl, P = _soft_problem()
+    m0 = energy.normalize(wl.m0[P.mag_nodes])
+    h = P.units.field_int([0.05, 0.0, 0.02])
+    jmax = 3
+    r = ncg.minimize(P, m0, h, ncg.Params(jmax=jmax))
+    st = r.stats
+    assert r.status == "converged"
+    assert st["evals"] == 2 * st["nli"] + 1 + st["ls_extra"]
+    assert st["li"] <= jmax * (st["nli"] + 1)
+    np.testing.assert_allclose(np.linalg.norm(r.m, axis=1), 1.0, atol=1e-14)
+    # energy never increases along the iterates
+    Fs = []
+    for k in range(1, 8):
+        rk = ncg.minimize(P, m0, h, ncg.Params(jmax=jmax, max_iter=k))
+        Fs.append(rk.F)
+    assert all(Fs[i + 1] <= Fs[i] for i in range(len(Fs) - 1))
+    # t3 holds at the returned state
+    assert np.abs(r.g).max() < 1e-10 ** (1 / 3) * (1 + abs(r.F))
+
+
+def test_preconditioning_reduces_evaluations():
+    """Sec. 3.2: a few inner steps cut the number of evaluations relative to
+    j_max = 0 (no preconditioning)."""
+    wl, P = _soft_problem()
+    m0 = energy.normalize(wl.m0[P.mag_nodes])
+    h = P.units.field_int([0.05, 0.0, 0.02])
+    r0 = ncg.minimize(P, m0, h, ncg.Params(jmax=0))
+    r4 = ncg.minimize(P, m0, h, ncg.Params(jmax=4))
+    assert r4.stats["evals"] < r0.stats["evals"]
+    assert r4.F == pytest.approx(r0.F, rel=1e-6)
+
+
+def test_paper_tables_consistent_with_line_search_reading():
+    """Tables 1, 2 and 4: evals = 2 nli + n_fields up to a small excess (the
+    rare extra line-search evaluations) and li close to at most
+    j_max (nli + n_fields), with equality when every inner solve runs to
+    j_max (Table 1 j_max = 2, Table 2 j_max = 4).  Table 4 j_max = 2 prints
+    li 0.3% above that bound, so the bound is checked to within 0.5%."""
+    rows = np.loadtxt(GOLDEN, comments="#", dtype=np.int64)
+    for tab, jm, evals, nli, li, nf in rows:
+        extra = evals - (2 * nli + nf)
+        assert 0 <= extra <= 0.005 * evals, (tab, jm)
+        assert li <= 1.005 * jm * (nli + nf), (tab, jm)
+    exact = {(1, 2), (2, 4)}
+    for tab, jm, evals, nli, li, nf in rows:
+        if (tab, jm) in exact:
+            assert li == jm * (nli + nf)
+
+
+def test_coercive_field_interpolation():
+    fields = np.array([[0, 0, 0.0], [0, 0, -1.0], [0, 0, -2.0], [0, 0, -3.0]])
+    M = np.array([[0, 0, 1.0], [0, 0, 0.5], [0, 0, -0.5], [0, 0, -1.0]])
+    assert curve.coercive_field(fields, M) == pytest.approx(1.5)
+    assert curve.coercive_field(fields, np.abs(M)) is None
+
+
+def test_stoner_wohlfarth_curve():
+    P, bsw = _sw_problem()
+    fields = np.stack([np.zeros(9), np.zeros(9), -bsw * np.linspace(0.96, 1.04, 9)], axis=1)
+    m0 = np.tile([0.0, 0.0, 1.0], (P.n_nodes, 1))
+    res = curve.demag_curve(P, fields, m0, ncg.Params(jmax=4))
+    assert abs(res["Hc_T"] - bsw) <= 0.01 * bsw
+    assert all(rec["status"] == "converged" for rec in res["records"])

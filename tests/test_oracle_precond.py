@@ -1,0 +1,123 @@
+"""Pins of the approximate-Hessian preconditioner (Eq. precond) and its
+truncated solve (Algorithm 1 with li1-li3)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import fem, energy, precond
+
+
+def _problem_no_demag(seed=6):
+    t = np.radians(30.0)
+    wl = synth.small_cube(n_mag=3, h=1.5e-9, Ms=1.0e6, A=1.0e-11, K1=2.0e6,
+                          axis=(np.sin(t), 0.0, np.cos(t)), jitter=0.07, seed=seed)
+    P = fem.assemble_workload(wl)
+    P.D = sp.csr_matrix(P.D.shape)          # magnetostatics off
+    return wl, P
+
+
+def _proj_grad(P, m, h):
+    """Pi_{m perp} grad F at (not normalised) m, no magnetostatics."""
+    grad = energy.gradient(P, m, np.zeros(P.n_phi), h)
+    lam = np.sum(m * grad, axis=1)
+    return grad - lam[:, None] * m
+
+
+def test_full_operator_is_derivative_of_projected_gradient():
+    """With all four terms and no magnetostatics, Eq. (precond) is the exact
+    Hessian-of-the-Lagrangian action (Eq. hessact), i.e. the directional
+    derivative of m -> Pi_{m perp} grad F(m)."""
+    wl, P = _problem_no_demag()
+    rng = np.random.default_rng(0)
+    m = energy.normalize(rng.normal(size=(P.n_mag, 3)))
+    v = rng.normal(size=(P.n_mag, 3))
+    h = P.units.field_int([0.3, 0.1, -0.2])
+    grad = energy.gradient(P, m, np.zeros(P.n_phi), h)
+    Hv = precond.apply_H(P, m, grad, v, keep_last=True)
+    eps = 1e-4
+    fd = (_proj_grad(P, m + eps * v, h) - _proj_grad(P, m - eps * v, h)) / (2 * eps)
+    np.testing.assert_allclose(Hv, fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
+
+
+def test_default_operator_drops_last_term():
+    wl, P = _problem_no_demag()
+    rng = np.random.default_rng(1)
+    m = energy.normalize(rng.normal(size=(P.n_mag, 3)))
+    v = rng.normal(size=(P.n_mag, 3))
+    grad = energy.gradient(P, m, np.zeros(P.n_phi), P.units.field_int([0, 0, 0.5]))
+    d = precond.apply_H(P, m, grad, v) - precond.apply_H(P, m, grad, v, keep_last=True)
+    np.testing.assert_allclose(d, np.sum(v * grad, axis=1, keepdims=True) * m, atol=1e-10)
+
+
+def test_tangent_vectors_stay_tangent():
+    wl, P = _problem_no_demag()
+    rng = np.random.default_rng(2)
+    m = energy.normalize(rng.normal(size=(P.n_mag, 3)))
+    v = energy.project(m, rng.normal(size=(P.n_mag, 3)))
+    grad = energy.gradient(P, m, np.zeros(P.n_phi), P.units.field_int([0.1, 0, 0]))
+    Hv = precond.apply_H(P, m, grad, v)
+    assert np.abs(np.sum(Hv * m, axis=1)).max() < 1e-10 * np.abs(Hv).max()
+    g = energy.project(m, grad)
+    y, _ = precond.precond_solve(P, m, grad, g, jmax=7)
+    assert np.abs(np.sum(y * m, axis=1)).max() < 1e-10 * np.abs(y).max()
+
+
+def test_converged_solve_matches_dense_tangent_system():
+    """m along a strong aligning field: H is SPD on the tangent space, and
+    many inner steps reproduce the dense solve there."""
+    wl, P = _problem_no_demag()
+    rng = np.random.default_rng(3)
+    m = energy.normalize(np.tile([0.0, 0.0, 1.0], (P.n_mag, 1)) + 0.2 * rng.normal(size=(P.n_mag, 3)))
+    h = P.units.field_int([0.0, 0.0, 8.0])
+    grad = energy.gradient(P, m, np.zeros(P.n_phi), h)
+    g = energy.project(m, grad)
+    y, steps = precond.precond_solve(P, m, grad, g, jmax=2000)
+    # dense tangent basis: two unit vectors orthogonal to each m_i
+    n = P.n_mag
+    t1 = energy.normalize(np.cross(m, [1.0, 0.3, 0.1]))
+    t2 = np.cross(m, t1)
+    B = np.zeros((3 * n, 2 * n))
+    for i in range(n):
+        B[3 * i:3 * i + 3, 2 * i] = t1[i]
+        B[3 * i:3 * i + 3, 2 * i + 1] = t2[i]
+    Hd = np.zeros((3 * n, 3 * n))
+    for k in range(3 * n):
+        e = np.zeros(3 * n)
+        e[k] = 1
+        Hd[:, k] = precond.apply_H(P, m, grad, e.reshape(n, 3)).ravel()
+    Ht = B.T @ Hd @ B
+    assert np.allclose(Ht, Ht.T, atol=1e-10 * np.abs(Ht).max())
+    assert np.linalg.eigvalsh(0.5 * (Ht + Ht.T)).min() > 0
+    yt = np.linalg.solve(Ht, B.T @ g.ravel())
+    # li3 stops early; its forcing term bounds the relative residual
+    eta = min(0.5, np.sqrt(np.linalg.norm(g)))
+    res = np.linalg.norm(Ht @ (B.T @ y.ravel()) - B.T @ g.ravel()) / np.linalg.norm(g)
+    assert res < eta
+    assert steps >= 1
+    # the same Algorithm 1 run to a tight tolerance reaches the dense solution
+    from oracle.linear_cg import alg1
+    dinv = 1.0 / precond.jacobi_diag(P)
+    yy, _, why = alg1(lambda v: precond.apply_H(P, m, grad, v.reshape(n, 3)).ravel(),
+                      -g.ravel(), np.zeros(3 * n),
+                      lambda r: (r.reshape(n, 3) * dinv[:, None]).ravel(),
+                      1e-13 * np.linalg.norm(g), 5000, neg_curvature=True)
+    assert why == "tol"
+    np.testing.assert_allclose(yy, B @ yt, rtol=1e-8, atol=1e-9 * np.abs(yt).max())
+
+
+def test_jmax_zero_and_first_step_negative_curvature():
+    wl, P = _problem_no_demag()
+    rng = np.random.default_rng(4)
+    m = energy.normalize(rng.normal(size=(P.n_mag, 3)))
+    grad = energy.gradient(P, m, np.zeros(P.n_phi), np.zeros(3))
+    g = energy.project(m, grad)
+    y, steps = precond.precond_solve(P, m, grad, g, jmax=0)
+    np.testing.assert_array_equal(y, g)
+    assert steps == 0
+    # a huge anti-aligned multiplier makes H negative definite on tangents
+    fake_grad = grad + 1e6 * m
+    g2 = energy.project(m, fake_grad)
+    y2, steps2 = precond.precond_solve(P, m, fake_grad, g2, jmax=5)
+    assert steps2 == 1
+    np.testing.assert_array_equal(y2, g2)
