@@ -1,0 +1,317 @@
+"""Benchmark: NCG iterations per second of the preconditioned NCG minimiser
+over the field steps of a demagnetisation curve (Sec. 3.1, Algorithm 4).
+
+Workload (default): an Nd2Fe14B cube, 80 nm edge, 48^3 voxels of 6 jittered
+tetrahedra (117,649 magnetic nodes), easy axis 1 degree off z, in an air box
+of twice the edge (97^3 lattice, 857,375 potential unknowns, 5.3M tets);
+m0 = +z; field along -z from 0 to -8 T in 40 values.  One step = one field
+step of the curve: set the field, minimise by Algorithm 4 until t1-t3 hold.
+
+value: NCG iterations / s with everything resident on the device (summed
+over ranks, max time over ranks).  e2e: the same metric through the public
+API with host buffers: each step uploads m from pinned host memory, sets the
+field, minimises and reads m and the stats back.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NCG iters/s & demag-curve wall time vs plain FP64 GPU at equal energy tol"
+UNIT = "NCG it/s"
+
+
+def workload(name):
+    import synth
+    if name == "hard_cube":
+        return synth.hard_cube()
+    if name == "soft_cube":
+        return synth.soft_cube()
+    if name == "small":
+        return synth.hard_cube(n_mag=12, n_fields=40)
+    raise ValueError(name)
+
+
+def workload_desc(name, wl, sizes=None):
+    d = {"workload": f"{wl.name}: {name}", "n_nodes": wl.mesh.n_nodes, "n_tets": wl.mesh.n_tets,
+         "fields": f"{len(wl.fields)} values from {wl.fields[0].tolist()} to {wl.fields[-1].tolist()} T",
+         "precision": "plain FP64", "jmax": 4, "tau_F": 1e-10, "poisson_tol": 1e-10,
+         "l2": "working set larger than L2 (no flush needed)"}
+    if sizes:
+        d.update(sizes)
+    return d
+
+
+# ------------------------------------------------------------ algorithmic bytes
+def alg_bytes(st, sz):
+    """Bytes one minimisation launch must move at ideal reuse (every array
+    element read or written once per phase, neighbour gathers served from
+    cache), from the launch's own counters:
+      potential step (mi)   12 nnz_phi + 96 n_phi   (SELL val+col; z, d_old, d, q;
+                                                      phi, d, r, q, diag^-1 -> phi, r, z)
+      evaluation (evals)    12 nnz_phi + 64 nnz_mag + 48 n_phi + 208 n_mag
+                            (potential set-up incl. D m; energy/gradient pass)
+      trial point (evals-1) 112 n_mag
+      inner step (li)       12 nnz_mag + 352 n_mag  (H product + update)
+      per iteration (nli+1) 272 n_mag               (inner set-up + direction)
+    """
+    nphi, nm = sz["n_phi"], sz["n_mag"]
+    nzp, nzm = sz["nnz_phi"], sz["nnz_mag"]
+    per_pcg = 12 * nzp + 96 * nphi
+    per_eval = 12 * nzp + 64 * nzm + 48 * nphi + 208 * nm
+    per_trial = 112 * nm
+    per_inner = 12 * nzm + 352 * nm
+    per_iter = 272 * nm
+    return (st["mi"] * per_pcg + st["evals"] * per_eval + max(st["evals"] - 1, 0) * per_trial
+            + st["li"] * per_inner + (st["nli"] + 1) * per_iter)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, v in zip(names, r[2:]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median([r[0] for r in rows]), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(wl, max_iter, warm_iter=0):
+    """The CPU oracle as it stands: assemble, then Algorithm 4 at the first
+    field from m0 with the potential solved by Algorithm 1 (the same
+    algorithm as the GPU).  Returns (nli, seconds, description)."""
+    from oracle import fem, energy, ncg
+    P = fem.assemble_workload(wl)
+    m = energy.normalize(wl.m0[P.mag_nodes])
+    h = P.units.field_int(wl.fields[0])
+    phi = None
+    if warm_iter:
+        r = ncg.minimize(P, m, h, ncg.Params(jmax=4, poisson="cg", max_iter=warm_iter))
+        m, phi = r.m, r.phi
+    t0 = time.perf_counter()
+    r = ncg.minimize(P, m, h, ncg.Params(jmax=4, poisson="cg", max_iter=max_iter), phi0=phi)
+    dt = time.perf_counter() - t0
+    desc = (f"oracle Algorithm 4 at the first field of the same workload, {r.stats['nli']} NCG "
+            f"iteration(s) incl. the initial evaluation ({r.stats['evals']} evaluations, "
+            f"{r.stats['mi']} potential steps), assembly excluded")
+    return r.stats["nli"], dt, desc
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "soft_cube", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    K, W = args.steps, max(args.warmup, 0)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        wl = workload(args.workload)
+        nli, dt, desc = oracle_sample(wl, max_iter=K, warm_iter=W)
+        v = nli / dt
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": K, "warmup": W, "ms_per_step": 1000.0 * dt / max(nli, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload_desc(args.workload, wl),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    from paper_1801_03690_gb300 import Magnet, Params
+
+    wl = workload(args.workload)
+    fields = wl.fields
+    n_steps_needed = W + K
+    if n_steps_needed > len(fields):
+        raise SystemExit(f"--warmup + --steps must be <= {len(fields)} field steps")
+    prm = Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10)
+    mag = Magnet(device=local_rank)
+    mag.upload_workload(wl)
+    sz = mag.sizes()
+    stream = torch.cuda.ExternalStream(mag.stream, device=torch.device("cuda", local_rank))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident run
+    mag.set_magnetization(wl.m0)
+    for k in range(W):
+        mag.set_field(fields[k])
+        mag.minimize(prm)
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    nli = 0
+    kern_ms = 0.0
+    bytes_total = 0
+    statuses = []
+    per_step = []
+    for k in range(W, W + K):
+        mag.set_field(fields[k])
+        mag.minimize_async(prm)
+        st = mag.get_stats()
+        ms = mag.last_kernel_ms()
+        kern_ms += ms
+        bytes_total += alg_bytes(st, sz)
+        nli += st["nli"]
+        statuses.append(st["status"])
+        per_step.append({"field_T": float(fields[k][2]), "nli": st["nli"], "evals": st["evals"],
+                         "mi": st["mi"], "li": st["li"], "Mz": st["M"][2], "ms": ms})
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    nli_all = nli
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        n = torch.tensor([nli], device="cuda", dtype=torch.float64)
+        dist.all_reduce(n)
+        nli_all = int(n.item())
+    value = nli_all / (t_max / 1000.0)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        m_host = torch.empty((wl.mesh.n_nodes, 3), dtype=torch.float64).pin_memory()
+        m_host.copy_(torch.from_numpy(wl.m0))
+        mag.set_magnetization(m_host.numpy())
+        for k in range(W):
+            mag.set_field(fields[k])
+            mag.minimize(prm)
+        m_host.copy_(torch.from_numpy(mag.get_magnetization()))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nli_e = 0
+        for k in range(W, W + K):
+            mag.set_magnetization(m_host.numpy())
+            mag.set_field(fields[k])
+            st = mag.minimize(prm)
+            m_host.copy_(torch.from_numpy(mag.get_magnetization()))
+            nli_e += st["nli"]
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - t0
+        mbytes = wl.mesh.n_nodes * 3 * 8
+        e2e = {"value": nli_e / te, "unit": UNIT, "h2d_bytes_per_step": mbytes + 24,
+               "d2h_bytes_per_step": mbytes + 136}
+
+    if rank != 0:
+        return 0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    achieved = bytes_total / (kern_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(args.workload, wl, sz),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "k_solver",
+                     "peak_source": peak_src, "alg_bytes_per_launch": bytes_total / K,
+                     "kernel_ms_per_launch": kern_ms / K},
+        "demag_curve": {"form": "plain FP64", "fields_timed": K, "wall_s": t_max / 1000.0,
+                        "statuses": statuses, "per_step": per_step},
+        "gpu_launches": 2 * K,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if ck:
+        line["clocks"] = ck
+    if world == 1 and not args.no_cpu_baseline:
+        nli_c, dt_c, desc = oracle_sample(wl, max_iter=1)
+        line["cpu_baseline"] = {"value": nli_c / dt_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line))
+    mag.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * mmncg -- preconditioned nonlinear conjugate gradient (NCG) minimisation of
+ * the micromagnetic energy on P1 tetrahedral meshes, on one GB300 GPU.
+ *
+ * The method is that of Exl, Fischbacher, Kovacs, Oezelt, Gusenbauer and
+ * Schrefl, "Preconditioned nonlinear conjugate gradient method for
+ * micromagnetic energy minimization" (arXiv:1801.03690):
+ *   - Eq. (energy), Sec. 2.2: F(m) = 1/2 m^T C m - 1/2 h_d^T M m - h_ext^T M m,
+ *     C = C_A + C_K (exchange + anisotropy), magnetostatics from a scalar
+ *     potential in an air box (Sec. 3.1);
+ *   - Algorithm 4 with beta*ZA (Sec. 2.2), minimising F(N m) with the
+ *     projected gradient of Eqs. (nablaLF), (proj), (opt2);
+ *   - the sparse approximate-Hessian preconditioner, Eq. (precond), solved by
+ *     Algorithm 1 with Jacobi diag(C_A) and the exits li1-li3 (Sec. 3.1);
+ *   - the stopping rules t1-t3 (Sec. 3.1).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an int status: MM_OK (0), a negative MM_ERR_* code,
+ *     or a positive soft status (MM_NOT_CONVERGED, MM_STALLED).
+ *     mm_last_error() gives a message for the last failing call.
+ *   - Inputs are SI: coordinates in metres, Ms in A/m, A in J/m, K1 in J/m^3,
+ *     applied fields as mu0*H in tesla.  Energies are returned in joules.
+ *     Internally (and for the stopping rules t1-t3, which compare energies
+ *     against 1) lengths are in nm and energies in units of
+ *     mu0*Mref^2*(1 nm)^3, Mref = the largest Ms in the material table.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Host
+ *     output arrays are written in full before the call returns.
+ *   - Calls with the suffix _dev take device pointers owned by the caller
+ *     (never freed by the library) and enqueue work on the context's stream
+ *     without synchronising, unless stated otherwise.
+ *   - Per-node arrays are indexed by the caller's node ids, row-major [n][3].
+ *     Only magnetic nodes (vertices of a tetrahedron with Ms > 0) carry m;
+ *     other rows are ignored on input and written as 0 on output.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef MMNCG_H
+#define MMNCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MM_OK = 0,
+    MM_NOT_CONVERGED = 1,        /* max_iter reached before t1-t3 held         */
+    MM_STALLED = 2,              /* line search found no decrease; m unchanged */
+    MM_ERR_ARG = -1,             /* invalid argument (NULL, size, parameter)   */
+    MM_ERR_MESH = -2,            /* invalid mesh: index, degenerate tet, ...   */
+    MM_ERR_OOM = -3,             /* device allocation failed                   */
+    MM_ERR_CUDA = -4,            /* CUDA runtime error                         */
+    MM_ERR_NONFINITE = -5,       /* NaN/Inf met in an energy or reduction      */
+    MM_ERR_DEVICE_TIMEOUT = -6,  /* a device-side barrier wait ran out         */
+    MM_ERR_STATE = -7            /* call out of order (e.g. no mesh uploaded)  */
+};
+
+typedef struct mm_ctx mm_ctx;
+
+/* One row of the material table (one per region label).  Ms = 0 marks a
+ * non-magnetic region (air).  The easy axis need not be normalised. */
+typedef struct {
+    double Ms;        /* saturation magnetisation, A/m                       */
+    double A;         /* exchange constant, J/m                              */
+    double K1;        /* uniaxial anisotropy constant, J/m^3                 */
+    double axis[3];   /* easy axis                                           */
+} mm_material;
+
+typedef struct {
+    int device;           /* CUDA device ordinal                                 */
+    int blocks_per_sm;    /* persistent-kernel blocks per SM; 0 = occupancy max  */
+    void* stream;         /* cudaStream_t to run on; NULL = a private stream     */
+} mm_options;
+
+/* Parameters of Algorithm 4 (defaults from mm_default_params). */
+typedef struct {
+    double tau_F;          /* t1-t3 tolerance, Sec. 3.1 (default 1e-10)            */
+    int jmax;              /* li1: max inner steps of the preconditioner (4)       */
+    int max_iter;          /* NCG iteration cap per minimisation (10000)           */
+    double theta_max;      /* line-search cap on max_i |alpha d_i| (0.1)           */
+    double c1;             /* sufficient-decrease constant (1e-4)                  */
+    int max_backtrack;     /* extra line-search evaluations allowed (10)           */
+    int keep_last_term;    /* 1: keep the last term of Eq. (precond) (0)           */
+    double poisson_tol;    /* relative residual of the potential solve (1e-10)     */
+    int poisson_max_iter;  /* cap on potential-solve steps per evaluation (20000)  */
+} mm_params;
+
+/* Counters of one call, in the columns of Table 1 plus the energy. */
+typedef struct {
+    int64_t evals;         /* function evaluations                                */
+    int64_t nli;           /* nonlinear (NCG) iterations                          */
+    int64_t li;            /* products with H inside the preconditioner solves    */
+    int64_t mi;            /* products with K_phi inside the potential solves     */
+    int64_t ls_extra;      /* evaluations spent backtracking in the line search   */
+    int32_t status;        /* MM_OK / MM_NOT_CONVERGED / MM_STALLED / error       */
+    int32_t pad;
+    double F;              /* energy at the returned state, J                     */
+    double terms[4];       /* exchange, anisotropy, magnetostatic, Zeeman; J      */
+    double F_internal;     /* energy in internal units (what t1-t3 see)           */
+    double M[3];           /* sum_i w_i m_i / sum_i w_i (reduced magnetisation)   */
+} mm_stats;
+
+void mm_default_params(mm_params* p);
+
+/* Create a context on a device.  opt may be NULL (device 0, private stream). */
+int mm_create(mm_ctx** ctx, const mm_options* opt);
+void mm_destroy(mm_ctx* ctx);
+const char* mm_last_error(const mm_ctx* ctx);
+
+/* Upload a tetrahedral mesh with per-tet region labels and a material table,
+ * and assemble (on the GPU) every operator of Eq. (energy): the exchange
+ * stiffness, the lumped anisotropy blocks and Ms weights, the scalar-
+ * potential stiffness over magnet + air with phi = 0 on the outer surface of
+ * the mesh, and the divergence coupling.  Sec. 2.2 and 3.1.
+ *   xyz    [n_nodes][3] coordinates, m
+ *   tets   [n_tets][4] node ids (either orientation; degenerate -> MM_ERR_MESH)
+ *   region [n_tets] labels in [0, n_regions)
+ * Resets m to +z on every magnetic node and the field to zero.  May be
+ * called again to replace the mesh. */
+int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz,
+                   int64_t n_tets, const int32_t* tets, const int32_t* region,
+                   int32_t n_regions, const mm_material* materials);
+
+/* Sizes: magnetic nodes, potential unknowns, nonzeros of the two graphs. */
+int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi,
+             int64_t* nnz_mag, int64_t* nnz_phi);
+
+/* Magnetisation per node ([n_nodes][3]); normalised on entry (N m, Eq. opt2). */
+int mm_set_magnetization(mm_ctx* ctx, const double* m);
+int mm_get_magnetization(mm_ctx* ctx, double* m_out);
+/* Device variants: m_dev [n_nodes][3] doubles on the context's device. */
+int mm_set_magnetization_dev(mm_ctx* ctx, const double* m_dev);
+int mm_get_magnetization_dev(mm_ctx* ctx, double* m_dev);
+
+/* Uniform applied field mu0*H_ext in tesla (Eq. energy, last term). */
+int mm_set_field(mm_ctx* ctx, const double mu0h[3]);
+
+/* Minimise F at the current field from the current m by Algorithm 4 until
+ * t1-t3 hold (Sec. 3.1).  The potential solve is warm-started from the last
+ * potential.  p may be NULL (defaults).  Synchronises; fills *out (may be
+ * NULL) and returns its status. */
+int mm_minimize(mm_ctx* ctx, const mm_params* p, mm_stats* out);
+/* Enqueue the same minimisation without waiting; read it with mm_get_stats. */
+int mm_minimize_async(mm_ctx* ctx, const mm_params* p);
+/* Wait for the context's stream and return the stats of the last
+ * minimisation or evaluation. */
+int mm_get_stats(mm_ctx* ctx, mm_stats* out);
+
+/* Energy of m (host [n_nodes][3], or NULL for the current m) at the current
+ * field: solves the potential (Sec. 3.1) and evaluates Eq. (energy).
+ * F in J; terms (may be NULL) = exchange, anisotropy, magnetostatic, Zeeman. */
+int mm_energy(mm_ctx* ctx, const double* m, const mm_params* p, double* F,
+              double terms[4]);
+/* Gradient of F at m (host or NULL = current), [n_nodes][3], internal units
+ * (energy unit per unit of m).  projected = 1 returns Pi_{m perp} grad F
+ * (Eqs. nablaLF, proj). */
+int mm_gradient(mm_ctx* ctx, const double* m, const mm_params* p,
+                double* grad_out, int projected);
+
+/* Scalar potential of the last evaluation, [n_nodes] (0 on the outer
+ * surface), internal units (Mref * 1 nm). */
+int mm_get_potential(mm_ctx* ctx, double* phi_out);
+
+/* Truncated preconditioner solve of Eq. (precond) by Algorithm 1 with
+ * li1-li3 (Sec. 2.2, 3.1) at the state of the last evaluation (mm_energy or
+ * mm_gradient): y ~ H(m)^{-1} g for the projected gradient g there.
+ * y_out [n_nodes][3]; *steps (may be NULL) = products with H. */
+int mm_precond_solve(mm_ctx* ctx, const mm_params* p, double* y_out,
+                     int64_t* steps);
+
+/* One product with the approximate Hessian of Eq. (precond) at the state of
+ * the last evaluation: out = H(m) v, v and out [n_nodes][3] host arrays. */
+int mm_hessian_apply(mm_ctx* ctx, const mm_params* p, const double* v,
+                     double* out);
+
+/* One product with the scalar-potential stiffness (Sec. 3.1):
+ * out = K_phi v on the unknowns, with v and out [n_nodes] host arrays
+ * (entries on the outer surface are ignored / written as 0). */
+int mm_potential_matvec(mm_ctx* ctx, const double* v, double* out);
+
+/* Demagnetisation curve (Sec. 3.1): for each of n_fields applied fields
+ * mu0*H (tesla, [n_fields][3]) set the field and minimise from the previous
+ * minimum.  stats_out [n_fields] (may be NULL).  Returns the first non-OK
+ * status met, after running every field. */
+int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields,
+                   const mm_params* p, mm_stats* stats_out);
+
+/* Device time (ms) of the last persistent-kernel launch, from CUDA events
+ * on the context's stream; synchronises. */
+int mm_last_kernel_ms(mm_ctx* ctx, double* ms);
+
+/* The stream the context runs on (a cudaStream_t). */
+void* mm_stream(const mm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMNCG_H */

@@ -1,0 +1,212 @@
+"""Python binding of the mmncg C-ABI (include/mmncg.h).
+
+Argument marshalling only: numpy arrays (host) or torch CUDA tensors (device
+pointers) are handed to the CUDA library, which runs every step of the
+method.  There is no CPU fallback: if the library is missing or no GPU is
+present, construction raises.
+"""
+import ctypes as C
+from dataclasses import dataclass, fields as dc_fields
+
+import numpy as np
+
+from . import _lib as L
+
+
+class MMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{L.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+@dataclass
+class Params:
+    """Parameters of Algorithm 4 (see mm_params in include/mmncg.h)."""
+    tau_F: float = 1e-10
+    jmax: int = 4
+    max_iter: int = 10000
+    theta_max: float = 0.1
+    c1: float = 1e-4
+    max_backtrack: int = 10
+    keep_last_term: bool = False
+    poisson_tol: float = 1e-10
+    poisson_max_iter: int = 20000
+
+    def to_c(self):
+        p = L.mm_params()
+        for f in dc_fields(self):
+            v = getattr(self, f.name)
+            setattr(p, f.name, int(v) if isinstance(v, (bool, int)) else float(v))
+        return p
+
+
+def _stats_dict(s):
+    return {"evals": s.evals, "nli": s.nli, "li": s.li, "mi": s.mi, "ls_extra": s.ls_extra,
+            "status": L.STATUS_NAMES.get(s.status, s.status), "status_code": s.status,
+            "F": s.F, "terms": list(s.terms), "F_internal": s.F_internal, "M": list(s.M)}
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Magnet:
+    """One micromagnetic problem on one GPU."""
+
+    def __init__(self, device=0, blocks_per_sm=0, stream=None):
+        self._lib = L.load()
+        opt = L.mm_options(device=device, blocks_per_sm=blocks_per_sm,
+                           stream=C.c_void_p(stream) if stream else None)
+        h = C.c_void_p()
+        rc = self._lib.mm_create(C.byref(h), C.byref(opt))
+        if rc != 0:
+            raise MMError(rc, "mm_create failed (no CUDA device, or no cooperative launch)")
+        self._h = h
+        self.n_nodes = 0
+
+    # ------------------------------------------------------------------ util
+    def _check(self, rc, soft_ok=False):
+        if rc < 0 or (rc > 0 and not soft_ok):
+            raise MMError(rc, self._lib.mm_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self):
+        return self._lib.mm_stream(self._h)
+
+    # ------------------------------------------------------------------ mesh
+    def upload_mesh(self, xyz, tets, region, materials):
+        xyz = _f64(xyz)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        region = np.ascontiguousarray(region, dtype=np.int32)
+        mats = np.asarray(materials, dtype=np.float64).reshape(-1, 6)
+        marr = (L.mm_material * len(mats))()
+        for r, row in enumerate(mats):
+            marr[r].Ms, marr[r].A, marr[r].K1 = row[0], row[1], row[2]
+            marr[r].axis[0], marr[r].axis[1], marr[r].axis[2] = row[3], row[4], row[5]
+        self._check(self._lib.mm_upload_mesh(self._h, xyz.shape[0], _ptr(xyz), tets.shape[0],
+                                             _ptr(tets), _ptr(region), len(mats), marr))
+        self.n_nodes = int(xyz.shape[0])
+        return self
+
+    def upload_workload(self, wl):
+        return self.upload_mesh(wl.mesh.xyz, wl.mesh.tets, wl.mesh.region, wl.materials)
+
+    def sizes(self):
+        v = [C.c_int64() for _ in range(4)]
+        self._check(self._lib.mm_sizes(self._h, *[C.byref(x) for x in v]))
+        return {"n_mag": v[0].value, "n_phi": v[1].value, "nnz_mag": v[2].value, "nnz_phi": v[3].value}
+
+    # ----------------------------------------------------------------- state
+    def set_magnetization(self, m):
+        m = _f64(m, (self.n_nodes, 3))
+        self._check(self._lib.mm_set_magnetization(self._h, _ptr(m)))
+
+    def get_magnetization(self):
+        out = np.zeros((self.n_nodes, 3))
+        self._check(self._lib.mm_get_magnetization(self._h, _ptr(out)))
+        return out
+
+    def set_magnetization_dev(self, t):
+        """t: contiguous float64 CUDA tensor [n_nodes, 3]."""
+        assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous()
+        self._check(self._lib.mm_set_magnetization_dev(self._h, C.c_void_p(t.data_ptr())))
+
+    def get_magnetization_dev(self, t):
+        assert t.is_cuda and t.is_contiguous()
+        self._check(self._lib.mm_get_magnetization_dev(self._h, C.c_void_p(t.data_ptr())))
+
+    def set_field(self, mu0h):
+        b = (C.c_double * 3)(*[float(x) for x in mu0h])
+        self._check(self._lib.mm_set_field(self._h, b))
+
+    # ------------------------------------------------------------ operations
+    def minimize(self, params=None):
+        p = (params or Params()).to_c()
+        s = L.mm_stats()
+        rc = self._lib.mm_minimize(self._h, C.byref(p), C.byref(s))
+        self._check(rc, soft_ok=True)
+        return _stats_dict(s)
+
+    def minimize_async(self, params=None):
+        p = (params or Params()).to_c()
+        self._check(self._lib.mm_minimize_async(self._h, C.byref(p)))
+
+    def get_stats(self):
+        s = L.mm_stats()
+        rc = self._lib.mm_get_stats(self._h, C.byref(s))
+        self._check(rc, soft_ok=True)
+        return _stats_dict(s)
+
+    def energy(self, m=None, params=None):
+        p = (params or Params()).to_c()
+        F = C.c_double()
+        terms = (C.c_double * 4)()
+        mm = None if m is None else _f64(m, (self.n_nodes, 3))
+        self._check(self._lib.mm_energy(self._h, None if mm is None else _ptr(mm), C.byref(p),
+                                        C.byref(F), terms))
+        return F.value, list(terms)
+
+    def gradient(self, m=None, projected=False, params=None):
+        p = (params or Params()).to_c()
+        out = np.zeros((self.n_nodes, 3))
+        mm = None if m is None else _f64(m, (self.n_nodes, 3))
+        self._check(self._lib.mm_gradient(self._h, None if mm is None else _ptr(mm), C.byref(p),
+                                          _ptr(out), int(projected)))
+        return out
+
+    def potential(self):
+        out = np.zeros(self.n_nodes)
+        self._check(self._lib.mm_get_potential(self._h, _ptr(out)))
+        return out
+
+    def precond_solve(self, params=None):
+        p = (params or Params()).to_c()
+        out = np.zeros((self.n_nodes, 3))
+        steps = C.c_int64()
+        self._check(self._lib.mm_precond_solve(self._h, C.byref(p), _ptr(out), C.byref(steps)))
+        return out, steps.value
+
+    def hessian_apply(self, v, params=None):
+        p = (params or Params()).to_c()
+        v = _f64(v, (self.n_nodes, 3))
+        out = np.zeros((self.n_nodes, 3))
+        self._check(self._lib.mm_hessian_apply(self._h, C.byref(p), _ptr(v), _ptr(out)))
+        return out
+
+    def potential_matvec(self, v):
+        v = _f64(v, (self.n_nodes,))
+        out = np.zeros(self.n_nodes)
+        self._check(self._lib.mm_potential_matvec(self._h, _ptr(v), _ptr(out)))
+        return out
+
+    def demag_curve(self, fields, params=None):
+        f = _f64(fields).reshape(-1, 3)
+        p = (params or Params()).to_c()
+        st = (L.mm_stats * len(f))()
+        rc = self._lib.mm_demag_curve(self._h, len(f), _ptr(f), C.byref(p), st)
+        self._check(rc, soft_ok=True)
+        return [_stats_dict(s) for s in st]
+
+    def last_kernel_ms(self):
+        ms = C.c_double()
+        self._check(self._lib.mm_last_kernel_ms(self._h, C.byref(ms)))
+        return ms.value

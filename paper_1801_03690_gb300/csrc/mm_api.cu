@@ -1,0 +1,941 @@
+// C-ABI of the mmncg library (declared in include/mmncg.h): context,
+// mesh upload (host-side graph construction, GPU assembly), state transfer
+// and the launches of the persistent solver kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mmncg.h"
+#include "mm_assemble.cuh"
+#include "mm_internal.cuh"
+
+namespace mm {
+__global__ void k_solver(const __grid_constant__ Problem P);
+}
+
+namespace {
+
+constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
+
+// ------------------------------------------------------------ small kernels
+
+__global__ void k_set_m(int nm, const int* mag_nodes, const double* m_nodes, double* X, int* bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    const long long n = mag_nodes[i];
+    const double a = m_nodes[3 * n], b = m_nodes[3 * n + 1], c = m_nodes[3 * n + 2];
+    const double r = sqrt(a * a + b * b + c * c);
+    if (!(r > 0.0) || !isfinite(r)) {
+        atomicExch(bad, 1);
+        X[i] = 0.0;
+        X[nm + i] = 0.0;
+        X[2 * nm + i] = 1.0;
+        return;
+    }
+    X[i] = a / r;
+    X[nm + i] = b / r;
+    X[2 * nm + i] = c / r;
+}
+
+// out[node][3] = v[c*nm + i] for magnetic nodes (other rows untouched)
+__global__ void k_scatter3(int nm, const int* mag_nodes, const double* v, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    const long long n = mag_nodes[i];
+    out[3 * n] = v[i];
+    out[3 * n + 1] = v[nm + i];
+    out[3 * n + 2] = v[2 * nm + i];
+}
+
+__global__ void k_gather3(int nm, const int* mag_nodes, const double* in, double* v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    const long long n = mag_nodes[i];
+    v[i] = in[3 * n];
+    v[nm + i] = in[3 * n + 1];
+    v[2 * nm + i] = in[3 * n + 2];
+}
+
+__global__ void k_scatter1(int np, const int* node_of_phi, const unsigned char* ident, const double* v,
+                           double* out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    out[node_of_phi[p]] = ident[p] ? 0.0 : v[p];
+}
+
+__global__ void k_gather1(int np, const int* node_of_phi, const unsigned char* ident, const double* in,
+                          double* v) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    v[p] = ident[p] ? 0.0 : in[node_of_phi[p]];
+}
+
+__global__ void k_set_field(mm::DevState* st, double h0, double h1, double h2) {
+    st->h[0] = h0;
+    st->h[1] = h1;
+    st->h[2] = h2;
+}
+
+__global__ void k_set_cur(mm::DevState* st, int cur) { st->cur = cur; }
+
+inline int nblk(long long n, int b = 256) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+struct mm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nsm = 0;
+    int blocks = 0;
+    int blocks_per_sm_req = 0;
+    std::string err;
+    // mesh
+    bool has_mesh = false;
+    bool has_eval = false;
+    int64_t n_nodes = 0;
+    int nm = 0, nphi = 0;
+    long long nnzm = 0, nnzp = 0;         // padded SELL entries
+    long long nnzm_true = 0, nnzp_true = 0;
+    double Mref = 0.0;
+    double field_T[3] = {0, 0, 0};
+    std::vector<void*> allocs;            // device buffers of the mesh
+    mm::Problem P{};
+    mm::DevState* d_state = nullptr;      // device
+    mm::DevState* h_state = nullptr;      // pinned host
+    int* d_mag_nodes = nullptr;
+    int* d_node_of_phi = nullptr;
+    unsigned char* d_ident = nullptr;
+    double* d_stage = nullptr;            // [n_nodes][3] staging
+    int* d_flag = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+};
+
+namespace {
+
+int fail(mm_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail(ctx, MM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int dalloc(mm_ctx* ctx, T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, MM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    *p = (T*)q;
+    return MM_OK;
+}
+
+void free_mesh(mm_ctx* ctx) {
+    for (void* p : ctx->allocs) cudaFree(p);
+    ctx->allocs.clear();
+    ctx->P = mm::Problem{};
+    ctx->has_mesh = false;
+    ctx->has_eval = false;
+}
+
+mm::Params to_params(const mm_params* p) {
+    mm_params d;
+    mm_default_params(&d);
+    if (!p) p = &d;
+    mm::Params q;
+    q.tau_F = p->tau_F;
+    q.jmax = p->jmax;
+    q.max_iter = p->max_iter;
+    q.theta_max = p->theta_max;
+    q.c1 = p->c1;
+    q.max_backtrack = p->max_backtrack;
+    q.keep_last_term = p->keep_last_term;
+    q.poisson_tol = p->poisson_tol;
+    q.poisson_max_iter = p->poisson_max_iter;
+    return q;
+}
+
+int check_params(mm_ctx* ctx, const mm_params* p) {
+    if (!p) return MM_OK;
+    if (!(p->tau_F > 0.0) || !(p->tau_F < 1.0)) return fail(ctx, MM_ERR_ARG, "tau_F must be in (0, 1)");
+    if (p->jmax < 0) return fail(ctx, MM_ERR_ARG, "jmax must be >= 0");
+    if (p->max_iter < 0) return fail(ctx, MM_ERR_ARG, "max_iter must be >= 0");
+    if (!(p->theta_max > 0.0)) return fail(ctx, MM_ERR_ARG, "theta_max must be > 0");
+    if (!(p->c1 > 0.0 && p->c1 < 1.0)) return fail(ctx, MM_ERR_ARG, "c1 must be in (0, 1)");
+    if (p->max_backtrack < 0) return fail(ctx, MM_ERR_ARG, "max_backtrack must be >= 0");
+    if (!(p->poisson_tol > 0.0)) return fail(ctx, MM_ERR_ARG, "poisson_tol must be > 0");
+    if (p->poisson_max_iter < 1) return fail(ctx, MM_ERR_ARG, "poisson_max_iter must be >= 1");
+    return MM_OK;
+}
+
+// Build SELL-32 slice pointers and columns from row adjacency lists.
+void build_sell(const std::vector<std::vector<int>>& rows, std::vector<long long>& sptr,
+                std::vector<int>& col, long long& nnz_true) {
+    const long long n = (long long)rows.size();
+    const long long ns = (n + 31) / 32;
+    sptr.assign(ns + 1, 0);
+    nnz_true = 0;
+    for (long long s = 0; s < ns; ++s) {
+        size_t w = 0;
+        for (long long r = s * 32; r < std::min(n, s * 32 + 32); ++r) w = std::max(w, rows[r].size());
+        sptr[s + 1] = sptr[s] + 32ll * (long long)w;
+    }
+    col.assign(sptr[ns], 0);
+    for (long long s = 0; s < ns; ++s) {
+        const long long w = (sptr[s + 1] - sptr[s]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const long long r = s * 32 + l;
+            for (long long k = 0; k < w; ++k) {
+                int c;
+                if (r < n && k < (long long)rows[r].size()) {
+                    c = rows[r][k];
+                    ++nnz_true;
+                } else {
+                    c = (r < n) ? (int)r : 0;          // padding: own row, value 0
+                }
+                col[sptr[s] + 32 * k + l] = c;
+            }
+        }
+    }
+}
+
+template <class T>
+int upload(mm_ctx* ctx, T** dst, const T* src, size_t count) {
+    int rc = dalloc(ctx, dst, count);
+    if (rc) return rc;
+    if (count) CK_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return MM_OK;
+}
+
+int launch_solver(mm_ctx* ctx, int mode, const mm::Params& prm) {
+    ctx->P.prm = prm;
+    ctx->P.mode = mode;
+    CK_CUDA(cudaMemsetAsync(ctx->P.bar, 0, 64 * sizeof(unsigned), ctx->stream));
+    CK_CUDA(cudaMemsetAsync(ctx->P.err, 0, sizeof(int), ctx->stream));
+    void* args[] = {(void*)&ctx->P};
+    CK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
+    CK_CUDA(cudaLaunchCooperativeKernel((const void*)mm::k_solver, dim3(ctx->blocks), dim3(MM_BLOCK), args, 0,
+                                        ctx->stream));
+    CK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK_CUDA(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(mm::DevState), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    ctx->timed = true;
+    return MM_OK;
+}
+
+int finish(mm_ctx* ctx) {
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    int e = 0;
+    CK_CUDA(cudaMemcpy(&e, ctx->P.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e == mm::ST_TIMEOUT || ctx->h_state->status == mm::ST_TIMEOUT)
+        return fail(ctx, MM_ERR_DEVICE_TIMEOUT, "a device barrier wait ran out");
+    return MM_OK;
+}
+
+void fill_stats(mm_ctx* ctx, mm_stats* out) {
+    const mm::DevState& s = *ctx->h_state;
+    const double EJ = kMu0 * ctx->Mref * ctx->Mref * 1e-27;
+    out->evals = s.evals;
+    out->nli = s.nli;
+    out->li = s.li;
+    out->mi = s.mi;
+    out->ls_extra = s.ls_extra;
+    out->status = s.status;
+    out->pad = 0;
+    out->F = s.F * EJ;
+    for (int k = 0; k < 4; ++k) out->terms[k] = s.terms[k] * EJ;
+    out->F_internal = s.F;
+    for (int k = 0; k < 3; ++k) out->M[k] = s.M[k];
+}
+
+int status_code(int st) {
+    switch (st) {
+        case mm::ST_OK: return MM_OK;
+        case mm::ST_NOT_CONVERGED: return MM_NOT_CONVERGED;
+        case mm::ST_STALLED: return MM_STALLED;
+        case mm::ST_NONFINITE: return MM_ERR_NONFINITE;
+        case mm::ST_TIMEOUT: return MM_ERR_DEVICE_TIMEOUT;
+        default: return MM_ERR_STATE;
+    }
+}
+
+int need_mesh(mm_ctx* ctx) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!ctx->has_mesh) return fail(ctx, MM_ERR_STATE, "no mesh uploaded");
+    CK_CUDA(cudaSetDevice(ctx->device));
+    return MM_OK;
+}
+
+int set_m_from_stage(mm_ctx* ctx) {
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));   // h_state->cur is current after this
+    CK_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    k_set_m<<<nblk(ctx->nm), 256, 0, ctx->stream>>>(ctx->nm, ctx->d_mag_nodes, ctx->d_stage,
+                                                     ctx->P.X[ctx->h_state->cur], ctx->d_flag);
+    CK_CUDA(cudaGetLastError());
+    int bad = 0;
+    CK_CUDA(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->has_eval = false;
+    if (bad) return fail(ctx, MM_ERR_NONFINITE, "magnetisation has a zero or non-finite vector");
+    return MM_OK;
+}
+
+int eval_current(mm_ctx* ctx, const mm_params* p) {
+    int rc = check_params(ctx, p);
+    if (rc) return rc;
+    rc = launch_solver(ctx, mm::MODE_EVAL, to_params(p));
+    if (rc) return rc;
+    rc = finish(ctx);
+    if (rc) return rc;
+    ctx->has_eval = true;
+    if (!std::isfinite(ctx->h_state->F)) return fail(ctx, MM_ERR_NONFINITE, "non-finite energy");
+    return MM_OK;
+}
+
+int maybe_set_m(mm_ctx* ctx, const double* m) {
+    if (!m) return MM_OK;
+    CK_CUDA(cudaMemcpy(ctx->d_stage, m, (size_t)ctx->n_nodes * 3 * sizeof(double), cudaMemcpyHostToDevice));
+    return set_m_from_stage(ctx);
+}
+
+int copy_out3(mm_ctx* ctx, const double* dev_soa, double* host) {
+    CK_CUDA(cudaMemsetAsync(ctx->d_stage, 0, (size_t)ctx->n_nodes * 3 * sizeof(double), ctx->stream));
+    k_scatter3<<<nblk(ctx->nm), 256, 0, ctx->stream>>>(ctx->nm, ctx->d_mag_nodes, dev_soa, ctx->d_stage);
+    CK_CUDA(cudaGetLastError());
+    CK_CUDA(cudaMemcpyAsync(host, ctx->d_stage, (size_t)ctx->n_nodes * 3 * sizeof(double),
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mm_default_params(mm_params* p) {
+    if (!p) return;
+    p->tau_F = 1e-10;
+    p->jmax = 4;
+    p->max_iter = 10000;
+    p->theta_max = 0.1;
+    p->c1 = 1e-4;
+    p->max_backtrack = 10;
+    p->keep_last_term = 0;
+    p->poisson_tol = 1e-10;
+    p->poisson_max_iter = 20000;
+}
+
+int mm_create(mm_ctx** out, const mm_options* opt) {
+    if (!out) return MM_ERR_ARG;
+    *out = nullptr;
+    mm_ctx* ctx = new mm_ctx();
+    ctx->device = opt ? opt->device : 0;
+    ctx->blocks_per_sm_req = opt ? opt->blocks_per_sm : 0;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        delete ctx;
+        return MM_ERR_CUDA;
+    }
+    if (ctx->device < 0 || ctx->device >= ndev) {
+        delete ctx;
+        return MM_ERR_ARG;
+    }
+    auto bail = [&](int code) {
+        delete ctx;
+        return code;
+    };
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bail(MM_ERR_CUDA);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (!coop) return bail(MM_ERR_CUDA);
+    cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mm::k_solver, MM_BLOCK, 0) != cudaSuccess || bps < 1)
+        return bail(MM_ERR_CUDA);
+    if (ctx->blocks_per_sm_req > 0) bps = std::min(bps, ctx->blocks_per_sm_req);
+    ctx->blocks = bps * ctx->nsm;
+    if (opt && opt->stream) {
+        ctx->stream = (cudaStream_t)opt->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(MM_ERR_CUDA);
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->d_state, sizeof(mm::DevState)) != cudaSuccess) return bail(MM_ERR_OOM);
+    if (cudaMallocHost(&ctx->h_state, sizeof(mm::DevState)) != cudaSuccess) return bail(MM_ERR_OOM);
+    if (cudaMalloc(&ctx->d_flag, sizeof(int)) != cudaSuccess) return bail(MM_ERR_OOM);
+    std::memset(ctx->h_state, 0, sizeof(mm::DevState));
+    cudaMemset(ctx->d_state, 0, sizeof(mm::DevState));
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    *out = ctx;
+    return MM_OK;
+}
+
+void mm_destroy(mm_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_mesh(ctx);
+    if (ctx->d_state) cudaFree(ctx->d_state);
+    if (ctx->h_state) cudaFreeHost(ctx->h_state);
+    if (ctx->d_flag) cudaFree(ctx->d_flag);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char* mm_last_error(const mm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void* mm_stream(const mm_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tets, const int32_t* tets,
+                   const int32_t* region, int32_t n_regions, const mm_material* materials) {
+    if (!ctx) return MM_ERR_ARG;
+    if (!xyz || !tets || !region || !materials) return fail(ctx, MM_ERR_ARG, "null array");
+    if (n_nodes < 4 || n_tets < 1 || n_regions < 1) return fail(ctx, MM_ERR_ARG, "empty mesh");
+    if (n_nodes >= (1ll << 31) - 64 || n_tets >= (1ll << 31) / 4)
+        return fail(ctx, MM_ERR_ARG, "mesh too large for 32-bit indices");
+    CK_CUDA(cudaSetDevice(ctx->device));
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    free_mesh(ctx);
+    const long long N = n_nodes, T = n_tets;
+    // ---- validation
+    double Mref = 0.0;
+    std::vector<double> mat(6 * (size_t)n_regions);
+    for (int r = 0; r < n_regions; ++r) {
+        const mm_material& m = materials[r];
+        const double an = std::sqrt(m.axis[0] * m.axis[0] + m.axis[1] * m.axis[1] + m.axis[2] * m.axis[2]);
+        if (!std::isfinite(m.Ms) || !std::isfinite(m.A) || !std::isfinite(m.K1) || m.Ms < 0 || m.A < 0)
+            return fail(ctx, MM_ERR_ARG, "material %d: Ms, A must be finite and >= 0, K1 finite", r);
+        if (m.Ms > 0 && !(an > 0 && std::isfinite(an)))
+            return fail(ctx, MM_ERR_ARG, "material %d: easy axis must be non-zero", r);
+        mat[6 * r] = m.Ms;
+        mat[6 * r + 1] = m.A;
+        mat[6 * r + 2] = m.K1;
+        mat[6 * r + 3] = an > 0 ? m.axis[0] : 0.0;
+        mat[6 * r + 4] = an > 0 ? m.axis[1] : 0.0;
+        mat[6 * r + 5] = an > 0 ? m.axis[2] : 1.0;
+        Mref = std::max(Mref, m.Ms);
+    }
+    if (!(Mref > 0)) return fail(ctx, MM_ERR_ARG, "no magnetic material (all Ms = 0)");
+    for (long long i = 0; i < 3 * N; ++i)
+        if (!std::isfinite(xyz[i])) return fail(ctx, MM_ERR_MESH, "non-finite coordinate");
+    std::vector<long long> cnt(N + 1, 0);
+    for (long long e = 0; e < T; ++e) {
+        if (region[e] < 0 || region[e] >= n_regions) return fail(ctx, MM_ERR_MESH, "tet %lld: bad region", e);
+        for (int v = 0; v < 4; ++v) {
+            const int n = tets[4 * e + v];
+            if (n < 0 || n >= N) return fail(ctx, MM_ERR_MESH, "tet %lld: node index out of range", e);
+            for (int u = 0; u < v; ++u)
+                if (tets[4 * e + u] == n) return fail(ctx, MM_ERR_MESH, "tet %lld: repeated node", e);
+            cnt[n + 1]++;
+        }
+    }
+    // node -> incident tets, ascending tet order
+    for (long long n = 0; n < N; ++n) cnt[n + 1] += cnt[n];
+    std::vector<long long> nt_ptr = cnt;
+    std::vector<int> nt_idx(4 * T);
+    {
+        std::vector<long long> fillp(nt_ptr.begin(), nt_ptr.end() - 1);
+        for (long long e = 0; e < T; ++e)
+            for (int v = 0; v < 4; ++v) nt_idx[fillp[tets[4 * e + v]]++] = (int)e;
+    }
+    // magnetic nodes
+    std::vector<int> mag_of(N, -1), mag_nodes;
+    {
+        std::vector<char> ismag(N, 0);
+        for (long long e = 0; e < T; ++e)
+            if (mat[6 * region[e]] > 0)
+                for (int v = 0; v < 4; ++v) ismag[tets[4 * e + v]] = 1;
+        for (long long n = 0; n < N; ++n)
+            if (ismag[n]) {
+                mag_of[n] = (int)mag_nodes.size();
+                mag_nodes.push_back((int)n);
+            }
+    }
+    const int nm = (int)mag_nodes.size();
+    // outer surface: faces that belong to exactly one tet
+    std::vector<char> dirichlet(N, 0);
+    {
+        std::vector<std::array<int, 3>> faces;
+        faces.reserve(4 * T);
+        for (long long e = 0; e < T; ++e) {
+            const int* t = tets + 4 * e;
+            for (int skip = 0; skip < 4; ++skip) {
+                std::array<int, 3> f;
+                int q = 0;
+                for (int v = 0; v < 4; ++v)
+                    if (v != skip) f[q++] = t[v];
+                std::sort(f.begin(), f.end());
+                faces.push_back(f);
+            }
+        }
+        std::sort(faces.begin(), faces.end());
+        size_t i = 0;
+        while (i < faces.size()) {
+            size_t j = i + 1;
+            while (j < faces.size() && faces[j] == faces[i]) ++j;
+            if (j - i == 1)
+                for (int v = 0; v < 3; ++v) dirichlet[faces[i][v]] = 1;
+            else if (j - i > 2)
+                return fail(ctx, MM_ERR_MESH, "a face is shared by more than two tets");
+            i = j;
+        }
+    }
+    // potential numbering: magnetic nodes first (identity rows where on the
+    // outer surface), then free air nodes in ascending node id
+    std::vector<int> phi_of(N, -1), node_of_phi;
+    std::vector<unsigned char> ident;
+    for (int i = 0; i < nm; ++i) {
+        phi_of[mag_nodes[i]] = i;
+        node_of_phi.push_back(mag_nodes[i]);
+        ident.push_back(dirichlet[mag_nodes[i]] ? 1 : 0);
+    }
+    for (long long n = 0; n < N; ++n)
+        if (mag_of[n] < 0 && !dirichlet[n]) {
+            phi_of[n] = (int)node_of_phi.size();
+            node_of_phi.push_back((int)n);
+            ident.push_back(0);
+        }
+    const int nphi = (int)node_of_phi.size();
+    // adjacency lists
+    std::vector<std::vector<int>> prow(nphi), mrow(nm);
+    for (int p = 0; p < nphi; ++p) {
+        auto& r = prow[p];
+        if (ident[p]) {
+            r.push_back(p);
+            continue;
+        }
+        const int n = node_of_phi[p];
+        for (long long q = nt_ptr[n]; q < nt_ptr[n + 1]; ++q) {
+            const int e = nt_idx[q];
+            for (int v = 0; v < 4; ++v) {
+                const int pc = phi_of[tets[4ll * e + v]];
+                if (pc >= 0 && !ident[pc]) r.push_back(pc);
+            }
+        }
+        r.push_back(p);
+        std::sort(r.begin(), r.end());
+        r.erase(std::unique(r.begin(), r.end()), r.end());
+    }
+    for (int i = 0; i < nm; ++i) {
+        auto& r = mrow[i];
+        const int n = mag_nodes[i];
+        for (long long q = nt_ptr[n]; q < nt_ptr[n + 1]; ++q) {
+            const int e = nt_idx[q];
+            if (!(mat[6 * region[e]] > 0)) continue;
+            for (int v = 0; v < 4; ++v) r.push_back(mag_of[tets[4ll * e + v]]);
+        }
+        std::sort(r.begin(), r.end());
+        r.erase(std::unique(r.begin(), r.end()), r.end());
+    }
+    std::vector<long long> m_sptr, p_sptr;
+    std::vector<int> m_col, p_col;
+    long long nnzm_true = 0, nnzp_true = 0;
+    build_sell(mrow, m_sptr, m_col, nnzm_true);
+    build_sell(prow, p_sptr, p_col, nnzp_true);
+    mrow.clear();
+    prow.clear();
+    const long long nnzm = m_sptr.back(), nnzp = p_sptr.back();
+
+    // ---- device upload and assembly
+    int rc;
+    double *d_xyz, *d_mat, *d_vol, *d_grad;
+    int *d_tets, *d_region, *d_nt_idx, *d_mag_of, *d_phi_of;
+    long long* d_nt_ptr;
+    mm::Problem& P = ctx->P;
+    P.nm = nm;
+    P.nphi = nphi;
+    P.nnzm = nnzm;
+    // the mesh arrays only live for the assembly: allocate them last-freed
+    std::vector<void*> tmp_start(ctx->allocs);
+    if ((rc = upload(ctx, &d_xyz, xyz, 3 * N))) return rc;
+    if ((rc = upload(ctx, &d_tets, (const int*)tets, 4 * T))) return rc;
+    if ((rc = upload(ctx, &d_region, (const int*)region, T))) return rc;
+    if ((rc = upload(ctx, &d_mat, mat.data(), mat.size()))) return rc;
+    if ((rc = upload(ctx, &d_nt_ptr, nt_ptr.data(), nt_ptr.size()))) return rc;
+    if ((rc = upload(ctx, &d_nt_idx, nt_idx.data(), nt_idx.size()))) return rc;
+    if ((rc = upload(ctx, &d_mag_of, mag_of.data(), mag_of.size()))) return rc;
+    if ((rc = upload(ctx, &d_phi_of, phi_of.data(), phi_of.size()))) return rc;
+    if ((rc = dalloc(ctx, &d_vol, T))) return rc;
+    if ((rc = dalloc(ctx, &d_grad, 12 * T))) return rc;
+    const size_t n_tmp = ctx->allocs.size() - tmp_start.size();
+    // persistent arrays
+    long long *d_msp, *d_psp;
+    int *d_mcol, *d_pcol;
+    double *KA, *G, *B, *CK, *w, *dinvA, *Kp, *dinvP;
+    if ((rc = upload(ctx, &ctx->d_mag_nodes, mag_nodes.data(), mag_nodes.size()))) return rc;
+    if ((rc = upload(ctx, &ctx->d_node_of_phi, node_of_phi.data(), node_of_phi.size()))) return rc;
+    if ((rc = upload(ctx, &ctx->d_ident, ident.data(), ident.size()))) return rc;
+    if ((rc = upload(ctx, &d_msp, m_sptr.data(), m_sptr.size()))) return rc;
+    if ((rc = upload(ctx, &d_mcol, m_col.data(), m_col.size()))) return rc;
+    if ((rc = upload(ctx, &d_psp, p_sptr.data(), p_sptr.size()))) return rc;
+    if ((rc = upload(ctx, &d_pcol, p_col.data(), p_col.size()))) return rc;
+    if ((rc = dalloc(ctx, &KA, nnzm))) return rc;
+    if ((rc = dalloc(ctx, &G, 3 * nnzm))) return rc;
+    if ((rc = dalloc(ctx, &B, 3 * nnzm))) return rc;
+    if ((rc = dalloc(ctx, &CK, 6 * (size_t)nm))) return rc;
+    if ((rc = dalloc(ctx, &w, nm))) return rc;
+    if ((rc = dalloc(ctx, &dinvA, nm))) return rc;
+    if ((rc = dalloc(ctx, &Kp, nnzp))) return rc;
+    if ((rc = dalloc(ctx, &dinvP, nphi))) return rc;
+    CK_CUDA(cudaMemset(ctx->d_flag, 0, sizeof(int)));
+    mm::k_tet_geometry<<<nblk(T), 256, 0, ctx->stream>>>(T, d_xyz, d_tets, d_vol, d_grad, ctx->d_flag);
+    CK_CUDA(cudaGetLastError());
+    mm::AssembleArgs A;
+    A.nm = nm;
+    A.nphi = nphi;
+    A.Mref = Mref;
+    A.tets = d_tets;
+    A.region = d_region;
+    A.materials = d_mat;
+    A.vol = d_vol;
+    A.grad = d_grad;
+    A.nt_ptr = d_nt_ptr;
+    A.nt_idx = d_nt_idx;
+    A.mag_of = d_mag_of;
+    A.phi_of = d_phi_of;
+    A.mag_nodes = ctx->d_mag_nodes;
+    A.node_of_phi = ctx->d_node_of_phi;
+    A.phi_ident = ctx->d_ident;
+    A.m_sptr = d_msp;
+    A.m_col = d_mcol;
+    A.nnzm = nnzm;
+    A.KA = KA;
+    A.G = G;
+    A.B = B;
+    A.CK = CK;
+    A.w = w;
+    A.dinvA = dinvA;
+    A.p_sptr = d_psp;
+    A.p_col = d_pcol;
+    A.Kp = Kp;
+    A.dinvP = dinvP;
+    A.bad = ctx->d_flag;
+    mm::k_assemble_phi<<<nblk(nphi), 256, 0, ctx->stream>>>(A);
+    CK_CUDA(cudaGetLastError());
+    mm::k_assemble_mag<<<nblk(nm), 256, 0, ctx->stream>>>(A);
+    CK_CUDA(cudaGetLastError());
+    int bad = 0;
+    CK_CUDA(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    // free the assembly-only arrays
+    for (size_t k = 0; k < n_tmp; ++k) cudaFree(ctx->allocs[tmp_start.size() + k]);
+    ctx->allocs.erase(ctx->allocs.begin() + tmp_start.size(), ctx->allocs.begin() + tmp_start.size() + n_tmp);
+    if (bad == 1) {
+        free_mesh(ctx);
+        return fail(ctx, MM_ERR_MESH, "degenerate tetrahedron (zero volume)");
+    }
+    if (bad) {
+        free_mesh(ctx);
+        return fail(ctx, MM_ERR_MESH, "assembly failed (code %d)", bad);
+    }
+    P.m_sptr = d_msp;
+    P.m_col = d_mcol;
+    P.KA = KA;
+    P.G = G;
+    P.B = B;
+    P.CK = CK;
+    P.w = w;
+    P.dinvA = dinvA;
+    P.p_sptr = d_psp;
+    P.p_col = d_pcol;
+    P.Kp = Kp;
+    P.dinvP = dinvP;
+    // solver vectors
+    const size_t v3 = 3 * (size_t)nm;
+    for (int s = 0; s < MM_NSLOT; ++s) {
+        if ((rc = dalloc(ctx, &P.X[s], v3))) return rc;
+        if ((rc = dalloc(ctx, &P.GR[s], v3))) return rc;
+        if ((rc = dalloc(ctx, &P.GP[s], v3))) return rc;
+        if ((rc = dalloc(ctx, &P.LAM[s], nm))) return rc;
+    }
+    if ((rc = dalloc(ctx, &P.unorm, nm))) return rc;
+    if ((rc = dalloc(ctx, &P.d, v3))) return rc;
+    P.yout = nullptr;
+    if ((rc = dalloc(ctx, &P.isol, v3))) return rc;
+    if ((rc = dalloc(ctx, &P.ires, v3))) return rc;
+    if ((rc = dalloc(ctx, &P.iprec, v3))) return rc;
+    if ((rc = dalloc(ctx, &P.idir[0], v3))) return rc;
+    if ((rc = dalloc(ctx, &P.idir[1], v3))) return rc;
+    if ((rc = dalloc(ctx, &P.ihd, v3))) return rc;
+    if ((rc = dalloc(ctx, &P.phi, nphi))) return rc;
+    if ((rc = dalloc(ctx, &P.rhs, nm))) return rc;
+    if ((rc = dalloc(ctx, &P.pres, nphi))) return rc;
+    if ((rc = dalloc(ctx, &P.pprec, nphi))) return rc;
+    if ((rc = dalloc(ctx, &P.pdir[0], nphi))) return rc;
+    if ((rc = dalloc(ctx, &P.pdir[1], nphi))) return rc;
+    if ((rc = dalloc(ctx, &P.pq, nphi))) return rc;
+    if ((rc = dalloc(ctx, &P.partials, 2 * (size_t)MM_MAXRED * ctx->blocks))) return rc;
+    if ((rc = dalloc(ctx, &P.bar, 64))) return rc;
+    if ((rc = dalloc(ctx, &P.err, 1))) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_stage, 3 * (size_t)N))) return rc;
+    P.state = ctx->d_state;
+    // zero every solver vector once (directions are read with coefficient
+    // 0 only behind explicit branches, but keep them finite regardless)
+    auto z = [&](double* p, size_t n) { return cudaMemsetAsync(p, 0, n * sizeof(double), ctx->stream); };
+    for (int s = 0; s < MM_NSLOT; ++s) {
+        CK_CUDA(z(P.X[s], v3));
+        CK_CUDA(z(P.GR[s], v3));
+        CK_CUDA(z(P.GP[s], v3));
+        CK_CUDA(z(P.LAM[s], nm));
+    }
+    CK_CUDA(z(P.unorm, nm));
+    CK_CUDA(z(P.d, v3));
+    CK_CUDA(z(P.isol, v3));
+    CK_CUDA(z(P.ires, v3));
+    CK_CUDA(z(P.iprec, v3));
+    CK_CUDA(z(P.idir[0], v3));
+    CK_CUDA(z(P.idir[1], v3));
+    CK_CUDA(z(P.ihd, v3));
+    CK_CUDA(z(P.phi, nphi));
+    CK_CUDA(z(P.rhs, nm));
+    CK_CUDA(z(P.pres, nphi));
+    CK_CUDA(z(P.pprec, nphi));
+    CK_CUDA(z(P.pdir[0], nphi));
+    CK_CUDA(z(P.pdir[1], nphi));
+    CK_CUDA(z(P.pq, nphi));
+    ctx->n_nodes = N;
+    ctx->nm = nm;
+    ctx->nphi = nphi;
+    ctx->nnzm = nnzm;
+    ctx->nnzp = nnzp;
+    ctx->nnzm_true = nnzm_true;
+    ctx->nnzp_true = nnzp_true;
+    ctx->Mref = Mref;
+    ctx->has_mesh = true;
+    // initial state: m = +z, zero field, slot 0
+    std::memset(ctx->h_state, 0, sizeof(mm::DevState));
+    CK_CUDA(cudaMemsetAsync(ctx->d_state, 0, sizeof(mm::DevState), ctx->stream));
+    k_set_cur<<<1, 1, 0, ctx->stream>>>(ctx->d_state, 0);
+    k_set_field<<<1, 1, 0, ctx->stream>>>(ctx->d_state, 0.0, 0.0, 0.0);
+    ctx->field_T[0] = ctx->field_T[1] = ctx->field_T[2] = 0.0;
+    std::vector<double> mz(3 * (size_t)N, 0.0);
+    for (long long n = 0; n < N; ++n) mz[3 * n + 2] = 1.0;
+    CK_CUDA(cudaMemcpy(ctx->d_stage, mz.data(), mz.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return set_m_from_stage(ctx);
+}
+
+int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi, int64_t* nnz_mag, int64_t* nnz_phi) {
+    if (!ctx || !ctx->has_mesh) return MM_ERR_STATE;
+    if (n_mag) *n_mag = ctx->nm;
+    if (n_phi) *n_phi = ctx->nphi;
+    if (nnz_mag) *nnz_mag = ctx->nnzm_true;
+    if (nnz_phi) *nnz_phi = ctx->nnzp_true;
+    return MM_OK;
+}
+
+int mm_set_magnetization(mm_ctx* ctx, const double* m) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!m) return fail(ctx, MM_ERR_ARG, "null m");
+    return maybe_set_m(ctx, m);
+}
+
+int mm_set_magnetization_dev(mm_ctx* ctx, const double* m_dev) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!m_dev) return fail(ctx, MM_ERR_ARG, "null m");
+    CK_CUDA(cudaMemcpyAsync(ctx->d_stage, m_dev, (size_t)ctx->n_nodes * 3 * sizeof(double),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+    return set_m_from_stage(ctx);
+}
+
+int mm_get_magnetization(mm_ctx* ctx, double* m_out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!m_out) return fail(ctx, MM_ERR_ARG, "null output");
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    return copy_out3(ctx, ctx->P.X[ctx->h_state->cur], m_out);
+}
+
+int mm_get_magnetization_dev(mm_ctx* ctx, double* m_dev) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!m_dev) return fail(ctx, MM_ERR_ARG, "null output");
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    CK_CUDA(cudaMemsetAsync(m_dev, 0, (size_t)ctx->n_nodes * 3 * sizeof(double), ctx->stream));
+    k_scatter3<<<nblk(ctx->nm), 256, 0, ctx->stream>>>(ctx->nm, ctx->d_mag_nodes, ctx->P.X[ctx->h_state->cur],
+                                                        m_dev);
+    CK_CUDA(cudaGetLastError());
+    return MM_OK;
+}
+
+int mm_set_field(mm_ctx* ctx, const double mu0h[3]) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!mu0h) return fail(ctx, MM_ERR_ARG, "null field");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(mu0h[k])) return fail(ctx, MM_ERR_ARG, "non-finite field");
+    k_set_field<<<1, 1, 0, ctx->stream>>>(ctx->d_state, mu0h[0] / (kMu0 * ctx->Mref),
+                                          mu0h[1] / (kMu0 * ctx->Mref), mu0h[2] / (kMu0 * ctx->Mref));
+    CK_CUDA(cudaGetLastError());
+    for (int k = 0; k < 3; ++k) ctx->field_T[k] = mu0h[k];
+    ctx->has_eval = false;
+    return MM_OK;
+}
+
+int mm_minimize_async(mm_ctx* ctx, const mm_params* p) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if ((rc = check_params(ctx, p))) return rc;
+    rc = launch_solver(ctx, mm::MODE_MINIMIZE, to_params(p));
+    if (rc) return rc;
+    ctx->has_eval = true;
+    return MM_OK;
+}
+
+int mm_get_stats(mm_ctx* ctx, mm_stats* out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    rc = finish(ctx);
+    if (rc) return rc;
+    if (out) fill_stats(ctx, out);
+    return status_code(ctx->h_state->status);
+}
+
+int mm_minimize(mm_ctx* ctx, const mm_params* p, mm_stats* out) {
+    int rc = mm_minimize_async(ctx, p);
+    if (rc) return rc;
+    rc = mm_get_stats(ctx, out);
+    if (rc == MM_ERR_NONFINITE) fail(ctx, rc, "non-finite energy during minimisation");
+    return rc;
+}
+
+int mm_energy(mm_ctx* ctx, const double* m, const mm_params* p, double* F, double terms[4]) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if ((rc = maybe_set_m(ctx, m))) return rc;
+    if ((rc = eval_current(ctx, p))) return rc;
+    const double EJ = kMu0 * ctx->Mref * ctx->Mref * 1e-27;
+    if (F) *F = ctx->h_state->F * EJ;
+    if (terms)
+        for (int k = 0; k < 4; ++k) terms[k] = ctx->h_state->terms[k] * EJ;
+    return MM_OK;
+}
+
+int mm_gradient(mm_ctx* ctx, const double* m, const mm_params* p, double* grad_out, int projected) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!grad_out) return fail(ctx, MM_ERR_ARG, "null output");
+    if ((rc = maybe_set_m(ctx, m))) return rc;
+    if ((rc = eval_current(ctx, p))) return rc;
+    const int c = ctx->h_state->cur;
+    return copy_out3(ctx, projected ? ctx->P.GP[c] : ctx->P.GR[c], grad_out);
+}
+
+int mm_get_potential(mm_ctx* ctx, double* phi_out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!phi_out) return fail(ctx, MM_ERR_ARG, "null output");
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    CK_CUDA(cudaMemsetAsync(ctx->d_stage, 0, (size_t)ctx->n_nodes * sizeof(double), ctx->stream));
+    k_scatter1<<<nblk(ctx->nphi), 256, 0, ctx->stream>>>(ctx->nphi, ctx->d_node_of_phi, ctx->d_ident, ctx->P.phi,
+                                                          ctx->d_stage);
+    CK_CUDA(cudaGetLastError());
+    CK_CUDA(cudaMemcpyAsync(phi_out, ctx->d_stage, (size_t)ctx->n_nodes * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int mm_precond_solve(mm_ctx* ctx, const mm_params* p, double* y_out, int64_t* steps) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!y_out) return fail(ctx, MM_ERR_ARG, "null output");
+    if (!ctx->has_eval) return fail(ctx, MM_ERR_STATE, "no evaluation at the current state");
+    if ((rc = check_params(ctx, p))) return rc;
+    if ((rc = launch_solver(ctx, mm::MODE_PRECOND, to_params(p)))) return rc;
+    if ((rc = finish(ctx))) return rc;
+    if (steps) *steps = ctx->h_state->li;
+    const int c = ctx->h_state->cur;
+    return copy_out3(ctx, ctx->h_state->y_is_g ? ctx->P.GP[c] : ctx->P.isol, y_out);
+}
+
+int mm_hessian_apply(mm_ctx* ctx, const mm_params* p, const double* v, double* out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!v || !out) return fail(ctx, MM_ERR_ARG, "null array");
+    if (!ctx->has_eval) return fail(ctx, MM_ERR_STATE, "no evaluation at the current state");
+    if ((rc = check_params(ctx, p))) return rc;
+    CK_CUDA(cudaMemcpy(ctx->d_stage, v, (size_t)ctx->n_nodes * 3 * sizeof(double), cudaMemcpyHostToDevice));
+    k_gather3<<<nblk(ctx->nm), 256, 0, ctx->stream>>>(ctx->nm, ctx->d_mag_nodes, ctx->d_stage, ctx->P.idir[0]);
+    CK_CUDA(cudaGetLastError());
+    if ((rc = launch_solver(ctx, mm::MODE_HESS, to_params(p)))) return rc;
+    if ((rc = finish(ctx))) return rc;
+    return copy_out3(ctx, ctx->P.ihd, out);
+}
+
+int mm_potential_matvec(mm_ctx* ctx, const double* v, double* out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!v || !out) return fail(ctx, MM_ERR_ARG, "null array");
+    CK_CUDA(cudaMemcpy(ctx->d_stage, v, (size_t)ctx->n_nodes * sizeof(double), cudaMemcpyHostToDevice));
+    k_gather1<<<nblk(ctx->nphi), 256, 0, ctx->stream>>>(ctx->nphi, ctx->d_node_of_phi, ctx->d_ident,
+                                                         ctx->d_stage, ctx->P.pdir[0]);
+    CK_CUDA(cudaGetLastError());
+    if ((rc = launch_solver(ctx, mm::MODE_KPHI, to_params(nullptr)))) return rc;
+    if ((rc = finish(ctx))) return rc;
+    CK_CUDA(cudaMemsetAsync(ctx->d_stage, 0, (size_t)ctx->n_nodes * sizeof(double), ctx->stream));
+    k_scatter1<<<nblk(ctx->nphi), 256, 0, ctx->stream>>>(ctx->nphi, ctx->d_node_of_phi, ctx->d_ident, ctx->P.pq,
+                                                          ctx->d_stage);
+    CK_CUDA(cudaGetLastError());
+    CK_CUDA(cudaMemcpyAsync(out, ctx->d_stage, (size_t)ctx->n_nodes * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields, const mm_params* p, mm_stats* stats_out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (n_fields < 0 || (n_fields > 0 && !fields)) return fail(ctx, MM_ERR_ARG, "bad field list");
+    if ((rc = check_params(ctx, p))) return rc;
+    int first = MM_OK;
+    for (int64_t k = 0; k < n_fields; ++k) {
+        if ((rc = mm_set_field(ctx, fields + 3 * k))) return rc;
+        mm_stats st;
+        rc = mm_minimize(ctx, p, &st);
+        if (rc == MM_ERR_DEVICE_TIMEOUT || rc == MM_ERR_CUDA) return rc;
+        if (stats_out) stats_out[k] = st;
+        if (first == MM_OK && rc != MM_OK) first = rc;
+    }
+    return first;
+}
+
+int mm_last_kernel_ms(mm_ctx* ctx, double* ms) {
+    if (!ctx || !ms) return MM_ERR_ARG;
+    if (!ctx->timed) return fail(ctx, MM_ERR_STATE, "no kernel launched yet");
+    CK_CUDA(cudaEventSynchronize(ctx->ev1));
+    float f = 0.f;
+    CK_CUDA(cudaEventElapsedTime(&f, ctx->ev0, ctx->ev1));
+    *ms = f;
+    return MM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Internal data structures of the mmncg library (host and device).
+//
+// Layout in HBM (all FP64 unless stated):
+//   * magnetic nodes i in [0, nm): m, gradients, directions and the inner
+//     solve vectors are SoA 3-vectors, component c of node i at v[c*nm + i];
+//   * potential unknowns p in [0, nphi): the first nm are the magnetic nodes
+//     (same order), the rest are the air nodes off the outer surface.  A
+//     magnetic node on the outer surface keeps an identity row (phi = 0);
+//   * both sparse graphs are SELL-32: rows in slices of 32, each slice
+//     column-major with the slice's max row length, entry (row r, k) at
+//     sptr[r/32] + 32*k + r%32; padding entries point at their own row with
+//     value 0.  One warp reads one slice: every load of col/val is a single
+//     coalesced 128/256-byte transaction.
+#pragma once
+#include <cstdint>
+
+#define MM_BLOCK 256
+#define MM_SELL 32
+#define MM_MAXRED 16          // reduction values per phase
+#define MM_NSLOT 3            // state slots: current, trial t, trial s
+
+namespace mm {
+
+enum Mode : int {
+    MODE_MINIMIZE = 0,
+    MODE_EVAL = 1,
+    MODE_PRECOND = 2,
+    MODE_HESS = 3,
+    MODE_KPHI = 4,
+};
+
+enum DevStatus : int {
+    ST_RUNNING = -100,
+    ST_OK = 0,
+    ST_NOT_CONVERGED = 1,
+    ST_STALLED = 2,
+    ST_NONFINITE = -5,
+    ST_TIMEOUT = -6,
+};
+
+struct Params {
+    double tau_F;
+    int jmax;
+    int max_iter;
+    double theta_max;
+    double c1;
+    int max_backtrack;
+    int keep_last_term;
+    double poisson_tol;
+    int poisson_max_iter;
+};
+
+// Scalars written back by the kernel (block 0) and read by the host.
+struct DevState {
+    int cur;                 // index of the current slot
+    int status;
+    long long evals, nli, li, mi, ls_extra;
+    double F;                // internal units
+    double terms[4];         // exchange, anisotropy, demag, Zeeman (internal)
+    double M[3];             // weighted mean magnetisation of the current slot
+    double gmax;             // |g|_inf of the current slot
+    double h[3];             // reduced applied field
+    int y_is_g;              // 1 if the last preconditioner output is g itself
+    int pad;
+};
+
+struct Problem {
+    int nm;                  // magnetic nodes
+    int nphi;                // potential unknowns
+    // magnetic graph (SELL-32): exchange stiffness K_A, and the divergence
+    // coupling in both orientations: G(i, j) = D_{j i} (for D^T phi, row i a
+    // magnetic node, column j a potential unknown) and B(j, i) = D_{j i}
+    // (for D m, row j, column i); SoA by component, stride nnzm.
+    const long long* m_sptr;
+    const int* m_col;
+    long long nnzm;
+    const double* KA;
+    const double* G;
+    const double* B;
+    const double* CK;        // [6][nm]: xx, xy, xz, yy, yz, zz of C_K blocks
+    const double* w;         // [nm] lumped Ms weights
+    const double* dinvA;     // [nm] 1 / diag(C_A) (1 where zero)
+    // potential graph (SELL-32)
+    const long long* p_sptr;
+    const int* p_col;
+    const double* Kp;
+    const double* dinvP;     // [nphi] 1 / diag(K_phi)
+    // state slots
+    double* X[MM_NSLOT];     // [3][nm] unit vectors
+    double* GR[MM_NSLOT];    // [3][nm] grad F
+    double* GP[MM_NSLOT];    // [3][nm] projected gradient
+    double* LAM[MM_NSLOT];   // [nm] lambda = m . grad F
+    double* unorm;           // [nm] |x + a d| of the last trial point
+    double* d;               // [3][nm] NCG direction
+    double* yout;            // [3][nm] preconditioner output
+    // inner solve (Algorithm 1 on H)
+    double* isol;            // [3][nm]
+    double* ires;            // [3][nm] residual
+    double* iprec;           // [3][nm] Jacobi-preconditioned residual
+    double* idir[2];         // [3][nm] direction (double buffer)
+    double* ihd;             // [3][nm] H * direction
+    // potential solve (Algorithm 1 on K_phi)
+    double* phi;             // [nphi]
+    double* rhs;             // [nm] D m on the magnetic rows (zero elsewhere)
+    double* pres;            // [nphi] residual
+    double* pprec;           // [nphi] Jacobi-preconditioned residual
+    double* pdir[2];         // [nphi] direction (double buffer)
+    double* pq;              // [nphi] K_phi * direction
+    // team machinery
+    double* partials;        // [2][MM_MAXRED][nblocks]
+    unsigned* bar;           // [0] = arrival count, [32] = generation
+    int* err;                // device error flag
+    DevState* state;
+    Params prm;
+    int mode;
+};
+
+}  // namespace mm

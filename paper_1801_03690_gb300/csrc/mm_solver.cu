@@ -1,0 +1,811 @@
+// Persistent solver kernel: Algorithm 4 (projected preconditioned NCG) with
+// its two inner solvers (Algorithm 1 on the scalar-potential stiffness and
+// on the approximate Hessian of Eq. precond), run entirely on the device.
+//
+// One cooperative launch covers a whole minimisation.  The blocks form a
+// team that moves through phases separated by team barriers; every phase is
+// a grid-stride pass over rows (one thread per SELL-32 row) that also writes
+// per-block partial sums.  After a barrier every block reduces the same
+// partials in the same fixed order, so all blocks hold bit-identical scalars
+// and take the same branch at every decision (potential-solve convergence,
+// li1-li3, line-search branches, beta*ZA, t1-t3) without host round trips or
+// atomics on floating-point data.  Barrier waits are bounded: a wait that
+// runs out sets the device error flag and every block leaves the kernel.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "mm_internal.cuh"
+
+namespace mm {
+
+namespace {
+
+constexpr unsigned long long kBarrierTimeoutNs = 5000000000ull;  // 5 s per wait
+constexpr int kWarps = MM_BLOCK / 32;
+
+struct Team {
+    int nb;
+    int rank;
+    unsigned* count;
+    unsigned* gen;
+    int* err;
+    double* part;
+    int epoch;
+    bool dead;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Team barrier (sense by generation counter) with a bounded wait.
+__device__ bool team_sync(Team& t) {
+    __shared__ int s_err;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = t.gen;
+        volatile int* verr = t.err;
+        int e = *verr;
+        if (e == 0) {
+            unsigned g = *vgen;
+            __threadfence();
+            unsigned prev = atomicAdd(t.count, 1u);
+            if (prev == (unsigned)t.nb - 1u) {
+                atomicExch(t.count, 0u);
+                __threadfence();
+                atomicAdd(t.gen, 1u);
+            } else {
+                unsigned long long t0 = global_ns();
+                while (*vgen == g) {
+                    if (*verr) break;
+                    __nanosleep(40);
+                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                        atomicCAS(t.err, 0, (int)ST_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+            e = *verr;
+        }
+        s_err = e;
+    }
+    __syncthreads();
+    t.dead = (s_err != 0);
+    return !t.dead;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce NS sums and NX maxima over the team.  Deterministic: fixed order
+// within warps (shfl_down tree, lane 0), across warps (ascending) and across
+// blocks (ascending strided accumulation, then the same block tree).
+template <int NS, int NX>
+__device__ bool team_reduce(Team& t, double (&s)[NS > 0 ? NS : 1], double (&x)[NX > 0 ? NX : 1]) {
+    static_assert(NS + NX <= MM_MAXRED, "too many reduction values");
+    __shared__ double sh[MM_MAXRED][kWarps];
+    __shared__ double res[MM_MAXRED];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        double v = warp_sum(s[k]);
+        if (lane == 0) sh[k][warp] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+        double v = warp_max(x[k]);
+        if (lane == 0) sh[NS + k][warp] = v;
+    }
+    __syncthreads();
+    double* part = t.part + (size_t)(t.epoch & 1) * MM_MAXRED * t.nb;
+    if (threadIdx.x < NS + NX) {
+        const int k = threadIdx.x;
+        double a = sh[k][0];
+        for (int w = 1; w < kWarps; ++w) a = (k < NS) ? a + sh[k][w] : fmax(a, sh[k][w]);
+        part[(size_t)k * t.nb + t.rank] = a;
+    }
+    t.epoch++;
+    if (!team_sync(t)) return false;
+    // every block folds all partials identically
+#pragma unroll
+    for (int k = 0; k < NS + NX; ++k) {
+        const double* pk = part + (size_t)k * t.nb;
+        double a = (k < NS) ? 0.0 : 0.0;
+        for (int j = threadIdx.x; j < t.nb; j += MM_BLOCK) a = (k < NS) ? a + pk[j] : fmax(a, pk[j]);
+        a = (k < NS) ? warp_sum(a) : warp_max(a);
+        if (lane == 0) sh[k][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS + NX) {
+        const int k = threadIdx.x;
+        double a = sh[k][0];
+        for (int w = 1; w < kWarps; ++w) a = (k < NS) ? a + sh[k][w] : fmax(a, sh[k][w]);
+        res[k] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NS; ++k) s[k] = res[k];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) x[k] = res[NS + k];
+    __syncthreads();
+    return true;
+}
+
+struct Row {
+    long long base;
+    int width;
+};
+
+__device__ __forceinline__ Row sell_row(const long long* sptr, int r) {
+    const int s = r >> 5;
+    const long long b = sptr[s];
+    return {b + (r & 31), (int)((sptr[s + 1] - b) >> 5)};
+}
+
+#define ROWS(r, n) for (int r = t.rank * MM_BLOCK + (int)threadIdx.x; r < (n); r += t.nb * MM_BLOCK)
+
+struct SlotScalars {
+    double F, terms[4], gmax, dphi, xdiff, xmax, M[3];
+};
+
+struct Ctx {
+    const Problem* P;
+    Team t;
+    long long evals, nli, li, mi, ls_extra;
+    double h[3];
+    SlotScalars sl[MM_NSLOT];
+    int y_is_g;
+};
+
+// ---------------------------------------------------------------- phases
+
+// x_s = N(x_c + a d), |x_c + a d| kept for Eq. (opt2); max|x_s - x_c|, max|x_s|.
+__device__ bool ph_trial(Ctx& C, int c, int s, double a) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    double mx[2] = {0.0, 0.0};
+    double dummy[1] = {0.0};
+    const double* xc = P.X[c];
+    double* xs = P.X[s];
+    ROWS(i, nm) {
+        double u0 = xc[i] + a * P.d[i];
+        double u1 = xc[nm + i] + a * P.d[nm + i];
+        double u2 = xc[2 * nm + i] + a * P.d[2 * nm + i];
+        double n = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+        double v0 = u0 / n, v1 = u1 / n, v2 = u2 / n;
+        xs[i] = v0;
+        xs[nm + i] = v1;
+        xs[2 * nm + i] = v2;
+        P.unorm[i] = n;
+        mx[0] = fmax(mx[0], fmax(fabs(v0 - xc[i]), fmax(fabs(v1 - xc[nm + i]), fabs(v2 - xc[2 * nm + i]))));
+        mx[1] = fmax(mx[1], fmax(fabs(v0), fmax(fabs(v1), fabs(v2))));
+    }
+    if (!team_reduce<0, 2>(t, dummy, mx)) return false;
+    C.sl[s].xdiff = mx[0];
+    C.sl[s].xmax = mx[1];
+    return true;
+}
+
+// Potential-solve set-up: rhs = D x_s on the magnetic rows, r = rhs - K phi,
+// z = diag(K)^-1 r.  Sums: |rhs|^2, r.z, |r|^2.
+__device__ bool ph_pinit(Ctx& C, int s, double& bb, double& rz, double& rr) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const double* x = P.X[s];
+    double acc[3] = {0.0, 0.0, 0.0};
+    double dummy[1] = {0.0};
+    const long long nz = P.nnzm;
+    ROWS(p, P.nphi) {
+        Row rw = sell_row(P.p_sptr, p);
+        double kphi = 0.0;
+        for (int k = 0; k < rw.width; ++k) {
+            const long long e = rw.base + 32ll * k;
+            kphi += P.Kp[e] * P.phi[P.p_col[e]];
+        }
+        double bp = 0.0;
+        if (p < nm) {
+            Row mr = sell_row(P.m_sptr, p);
+            for (int k = 0; k < mr.width; ++k) {
+                const long long e = mr.base + 32ll * k;
+                const int j = P.m_col[e];
+                bp += P.B[e] * x[j] + P.B[nz + e] * x[nm + j] + P.B[2 * nz + e] * x[2 * nm + j];
+            }
+            P.rhs[p] = bp;
+        }
+        const double r = bp - kphi;
+        const double z = r * P.dinvP[p];
+        P.pres[p] = r;
+        P.pprec[p] = z;
+        acc[0] += bp * bp;
+        acc[1] += r * z;
+        acc[2] += r * r;
+    }
+    if (!team_reduce<3, 0>(t, acc, dummy)) return false;
+    bb = acc[0];
+    rz = acc[1];
+    rr = acc[2];
+    return true;
+}
+
+// q = K v with v_j = A_j + beta * Bv_j formed on the fly (the new CG
+// direction); v_p is stored to vout.  Sum: v . q.
+__device__ bool ph_pmatvec(Ctx& C, const double* A, const double* Bv, double beta,
+                           double* vout, double* q, double& vq) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    double acc[1] = {0.0};
+    double dummy[1] = {0.0};
+    const bool useB = (beta != 0.0);
+    ROWS(p, P.nphi) {
+        Row rw = sell_row(P.p_sptr, p);
+        double s = 0.0;
+        if (useB) {
+            for (int k = 0; k < rw.width; ++k) {
+                const long long e = rw.base + 32ll * k;
+                const int j = P.p_col[e];
+                s += P.Kp[e] * (A[j] + beta * Bv[j]);
+            }
+        } else {
+            for (int k = 0; k < rw.width; ++k) {
+                const long long e = rw.base + 32ll * k;
+                s += P.Kp[e] * A[P.p_col[e]];
+            }
+        }
+        const double vp = useB ? A[p] + beta * Bv[p] : A[p];
+        if (vout) vout[p] = vp;
+        q[p] = s;
+        acc[0] += vp * s;
+    }
+    if (!team_reduce<1, 0>(t, acc, dummy)) return false;
+    vq = acc[0];
+    return true;
+}
+
+// phi += a v; r -= a q; z = diag^-1 r.  Sums: r.z, |r|^2.
+__device__ bool ph_pupdate(Ctx& C, const double* v, double a, double& rz, double& rr) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    double acc[2] = {0.0, 0.0};
+    double dummy[1] = {0.0};
+    ROWS(p, P.nphi) {
+        P.phi[p] += a * v[p];
+        const double r = P.pres[p] - a * P.pq[p];
+        const double z = r * P.dinvP[p];
+        P.pres[p] = r;
+        P.pprec[p] = z;
+        acc[0] += r * z;
+        acc[1] += r * r;
+    }
+    if (!team_reduce<2, 0>(t, acc, dummy)) return false;
+    rz = acc[0];
+    rr = acc[1];
+    return true;
+}
+
+__device__ bool ph_pzero(Ctx& C) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    ROWS(p, P.nphi) {
+        P.phi[p] = 0.0;
+        P.pres[p] = 0.0;
+    }
+    return team_sync(t);
+}
+
+// Algorithm 1 on K_phi phi = D m (Sec. 3.1), warm-started from phi.
+__device__ bool solve_potential(Ctx& C, int s) {
+    const Problem& P = *C.P;
+    double bb, rz, rr;
+    if (!ph_pinit(C, s, bb, rz, rr)) return false;
+    if (bb == 0.0) return ph_pzero(C);
+    const double tol2 = P.prm.poisson_tol * P.prm.poisson_tol * bb;
+    double beta = 0.0;
+    int cb = 0;
+    long long k = 0;
+    while (rr >= tol2 && k < P.prm.poisson_max_iter) {
+        double pq;
+        if (!ph_pmatvec(C, P.pprec, P.pdir[cb], beta, P.pdir[1 - cb], P.pq, pq)) return false;
+        const double a = rz / pq;
+        double rzn;
+        if (!ph_pupdate(C, P.pdir[1 - cb], a, rzn, rr)) return false;
+        beta = rzn / rz;
+        rz = rzn;
+        cb = 1 - cb;
+        ++k;
+    }
+    C.mi += k;
+    return true;
+}
+
+// Energy and gradient pass (Eq. energy, nablaLF, proj, opt2) at slot s:
+// grad = C_A x + C_K x + D^T phi - w h; lambda = x . grad; g = grad - lambda x.
+__device__ bool ph_gradient(Ctx& C, int s, bool trial) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const long long nz = P.nnzm;
+    const double* x = P.X[s];
+    double* gr = P.GR[s];
+    double* gp = P.GP[s];
+    double* lamv = P.LAM[s];
+    const double h0 = C.h[0], h1 = C.h[1], h2 = C.h[2];
+    // sums: exchange, anisotropy, Zeeman, phi.rhs, phi.r, dphi, M0, M1, M2, sum w
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double mx[1] = {0.0};
+    ROWS(p, P.nphi) {
+        acc[4] += P.phi[p] * P.pres[p];
+        if (p < nm) {
+            const int i = p;
+            acc[3] += P.phi[i] * P.rhs[i];
+            Row rw = sell_row(P.m_sptr, i);
+            double c0 = 0, c1 = 0, c2 = 0, t0 = 0, t1 = 0, t2 = 0;
+            for (int k = 0; k < rw.width; ++k) {
+                const long long e = rw.base + 32ll * k;
+                const int j = P.m_col[e];
+                const double ka = P.KA[e];
+                c0 += ka * x[j];
+                c1 += ka * x[nm + j];
+                c2 += ka * x[2 * nm + j];
+                const double ph = P.phi[j];
+                t0 += P.G[e] * ph;
+                t1 += P.G[nz + e] * ph;
+                t2 += P.G[2 * nz + e] * ph;
+            }
+            const double x0 = x[i], x1 = x[nm + i], x2 = x[2 * nm + i];
+            const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
+            const double kyy = P.CK[3 * nm + i], kyz = P.CK[4 * nm + i], kzz = P.CK[5 * nm + i];
+            const double a0 = kxx * x0 + kxy * x1 + kxz * x2;
+            const double a1 = kxy * x0 + kyy * x1 + kyz * x2;
+            const double a2 = kxz * x0 + kyz * x1 + kzz * x2;
+            const double wi = P.w[i];
+            const double g0 = 2.0 * c0 + a0 + t0 - wi * h0;
+            const double g1 = 2.0 * c1 + a1 + t1 - wi * h1;
+            const double g2 = 2.0 * c2 + a2 + t2 - wi * h2;
+            acc[0] += x0 * c0 + x1 * c1 + x2 * c2;
+            acc[1] += 0.5 * (x0 * a0 + x1 * a1 + x2 * a2);
+            acc[2] -= wi * (h0 * x0 + h1 * x1 + h2 * x2);
+            const double lam = x0 * g0 + x1 * g1 + x2 * g2;
+            const double p0 = g0 - lam * x0, p1 = g1 - lam * x1, p2 = g2 - lam * x2;
+            gr[i] = g0;
+            gr[nm + i] = g1;
+            gr[2 * nm + i] = g2;
+            gp[i] = p0;
+            gp[nm + i] = p1;
+            gp[2 * nm + i] = p2;
+            lamv[i] = lam;
+            mx[0] = fmax(mx[0], fmax(fabs(p0), fmax(fabs(p1), fabs(p2))));
+            if (trial)
+                acc[5] += (p0 * P.d[i] + p1 * P.d[nm + i] + p2 * P.d[2 * nm + i]) / P.unorm[i];
+            acc[6] += wi * x0;
+            acc[7] += wi * x1;
+            acc[8] += wi * x2;
+            acc[9] += wi;
+        }
+    }
+    if (!team_reduce<10, 1>(t, acc, mx)) return false;
+    SlotScalars& S = C.sl[s];
+    S.terms[0] = acc[0];
+    S.terms[1] = acc[1];
+    S.terms[2] = 0.5 * (acc[3] + acc[4]);   // phi.b - 1/2 phi.K phi, K phi = b - r
+    S.terms[3] = acc[2];
+    S.F = ((S.terms[0] + S.terms[1]) + S.terms[2]) + S.terms[3];
+    S.dphi = acc[5];
+    S.gmax = mx[0];
+    S.M[0] = acc[6] / acc[9];
+    S.M[1] = acc[7] / acc[9];
+    S.M[2] = acc[8] / acc[9];
+    return true;
+}
+
+// One function evaluation at slot s: at x_c + a d (trial) or at x_s as is.
+__device__ bool evaluate(Ctx& C, int c, int s, bool trial, double a) {
+    if (trial && !ph_trial(C, c, s, a)) return false;
+    if (!solve_potential(C, s)) return false;
+    if (!ph_gradient(C, s, trial)) return false;
+    C.evals++;
+    return true;
+}
+
+// out = H(m) v with v_i = ca*A_i + cb*Bv_i formed on the fly (Eq. precond,
+// magnetostatics dropped; last term only if keep_last_term); v is stored to
+// vout if given.  Sum: v . Hv.
+__device__ bool ph_hess(Ctx& C, int s, const double* A, double ca, const double* Bv, double cb,
+                        double* vout, double* out, double& vHv) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const double* m = P.X[s];
+    const double* lamv = P.LAM[s];
+    const double* gr = P.GR[s];
+    const bool useB = (cb != 0.0);
+    const bool keep = P.prm.keep_last_term != 0;
+    double acc[1] = {0.0};
+    double dummy[1] = {0.0};
+    ROWS(i, nm) {
+        Row rw = sell_row(P.m_sptr, i);
+        double c0 = 0, c1 = 0, c2 = 0;
+        for (int k = 0; k < rw.width; ++k) {
+            const long long e = rw.base + 32ll * k;
+            const int j = P.m_col[e];
+            const double ka = P.KA[e];
+            double v0 = ca * A[j], v1 = ca * A[nm + j], v2 = ca * A[2 * nm + j];
+            if (useB) {
+                v0 += cb * Bv[j];
+                v1 += cb * Bv[nm + j];
+                v2 += cb * Bv[2 * nm + j];
+            }
+            c0 += ka * v0;
+            c1 += ka * v1;
+            c2 += ka * v2;
+        }
+        double v0 = ca * A[i], v1 = ca * A[nm + i], v2 = ca * A[2 * nm + i];
+        if (useB) {
+            v0 += cb * Bv[i];
+            v1 += cb * Bv[nm + i];
+            v2 += cb * Bv[2 * nm + i];
+        }
+        const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
+        const double kyy = P.CK[3 * nm + i], kyz = P.CK[4 * nm + i], kzz = P.CK[5 * nm + i];
+        const double Cv0 = 2.0 * c0 + (kxx * v0 + kxy * v1 + kxz * v2);
+        const double Cv1 = 2.0 * c1 + (kxy * v0 + kyy * v1 + kyz * v2);
+        const double Cv2 = 2.0 * c2 + (kxz * v0 + kyz * v1 + kzz * v2);
+        const double m0 = m[i], m1 = m[nm + i], m2 = m[2 * nm + i];
+        const double mc = m0 * Cv0 + m1 * Cv1 + m2 * Cv2;
+        const double lam = lamv[i];
+        double h0 = Cv0 - mc * m0 - lam * v0;
+        double h1 = Cv1 - mc * m1 - lam * v1;
+        double h2 = Cv2 - mc * m2 - lam * v2;
+        if (keep) {
+            const double vg = v0 * gr[i] + v1 * gr[nm + i] + v2 * gr[2 * nm + i];
+            h0 -= vg * m0;
+            h1 -= vg * m1;
+            h2 -= vg * m2;
+        }
+        if (vout) {
+            vout[i] = v0;
+            vout[nm + i] = v1;
+            vout[2 * nm + i] = v2;
+        }
+        out[i] = h0;
+        out[nm + i] = h1;
+        out[2 * nm + i] = h2;
+        acc[0] += v0 * h0 + v1 * h1 + v2 * h2;
+    }
+    if (!team_reduce<1, 0>(t, acc, dummy)) return false;
+    vHv = acc[0];
+    return true;
+}
+
+// Algorithm 1 for H(m_s) y = g_s, y_0 = 0, Jacobi diag(C_A), exits li1-li3.
+__device__ bool precond_solve(Ctx& C, int s) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const int jmax = P.prm.jmax;
+    if (jmax <= 0) {
+        C.y_is_g = 1;
+        return true;
+    }
+    const double* g = P.GP[s];
+    // residual gr = H*0 + b with b = -g; preconditioned yv; direction -yv
+    double acc[2] = {0.0, 0.0};
+    double dummy[1] = {0.0};
+    ROWS(i, nm) {
+        const double di = P.dinvA[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double r = -g[c * nm + i];
+            const double z = di * r;
+            P.ires[c * nm + i] = r;
+            P.iprec[c * nm + i] = z;
+            P.isol[c * nm + i] = 0.0;
+            acc[0] += r * z;
+            acc[1] += r * r;
+        }
+    }
+    if (!team_reduce<2, 0>(t, acc, dummy)) return false;
+    double gy = acc[0];
+    const double ng = sqrt(acc[1]);
+    const double eps = fmin(0.5, sqrt(ng)) * ng;
+    C.y_is_g = 0;
+    if (ng < eps) return true;                  // y = 0 (only when g = 0 ... eps = 0)
+    double beta = 0.0;
+    int cb = 0;
+    int steps = 0;
+    while (steps < jmax) {
+        double dHd;
+        // direction d = -yv + beta d_old, formed on the fly and stored
+        if (!ph_hess(C, s, P.iprec, -1.0, P.idir[cb], beta, P.idir[1 - cb], P.ihd, dHd)) return false;
+        ++steps;
+        C.li++;
+        if (dHd <= 0.0) {                       // li2
+            if (steps == 1) C.y_is_g = 1;
+            return true;
+        }
+        const double a = gy / dHd;
+        const double* dv = P.idir[1 - cb];
+        double a2[2] = {0.0, 0.0};
+        ROWS(i, nm) {
+            const double di = P.dinvA[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int q = c * nm + i;
+                P.isol[q] += a * dv[q];
+                const double r = P.ires[q] + a * P.ihd[q];
+                const double z = di * r;
+                P.ires[q] = r;
+                P.iprec[q] = z;
+                a2[0] += r * z;
+                a2[1] += r * r;
+            }
+        }
+        if (!team_reduce<2, 0>(t, a2, dummy)) return false;
+        if (sqrt(a2[1]) < eps) return true;     // li3
+        beta = a2[0] / gy;
+        gy = a2[0];
+        cb = 1 - cb;
+    }
+    return true;                                // li1
+}
+
+// beta*ZA dots between slot a (new gradient gn) and slot c (old gradient go)
+// with y the preconditioned gn and d the previous direction:
+//   y.gn, y.go, (gn-go).y, (gn-go).d, gn.d, gn.gn, gn.go, (gn-go).gn
+__device__ bool ph_dir_dots(Ctx& C, int a, int c, double (&dots)[8]) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const double* y = C.y_is_g ? P.GP[a] : P.isol;
+    const double* gn = P.GP[a];
+    const double* go = P.GP[c];
+    double dummy[1] = {0.0};
+    for (int k = 0; k < 8; ++k) dots[k] = 0.0;
+    ROWS(i, nm) {
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) {
+            const int q = q3 * nm + i;
+            const double yy = y[q], n = gn[q], o = go[q], dd = P.d[q];
+            const double dg = n - o;
+            dots[0] += yy * n;
+            dots[1] += yy * o;
+            dots[2] += dg * yy;
+            dots[3] += dg * dd;
+            dots[4] += n * dd;
+            dots[5] += n * n;
+            dots[6] += n * o;
+            dots[7] += dg * n;
+        }
+    }
+    return team_reduce<8, 0>(t, dots, dummy);
+}
+
+// d = -v + beta d (kind 1: v = y; kind 2: v = g; kind 3: d = -g), max_i |d_i|.
+__device__ bool ph_dir_write(Ctx& C, int a, int kind, double beta, double& dmax) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const double* y = C.y_is_g ? P.GP[a] : P.isol;
+    const double* v = (kind == 1) ? y : P.GP[a];
+    const double b = (kind == 3) ? 0.0 : beta;   // b == 0: d_old is not read
+    double mx[1] = {0.0};
+    double dummy[1] = {0.0};
+    ROWS(i, nm) {
+        double n2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int q = c * nm + i;
+            const double dn = (b == 0.0) ? -v[q] : -v[q] + b * P.d[q];
+            P.d[q] = dn;
+            n2 += dn * dn;
+        }
+        mx[0] = fmax(mx[0], sqrt(n2));
+    }
+    if (!team_reduce<0, 1>(t, dummy, mx)) return false;
+    dmax = mx[0];
+    return true;
+}
+
+__device__ __forceinline__ double beta_za(double y_gn, double y_go, double dg_y, double dg_d) {
+    if (y_gn > y_go) return (dg_d == 0.0) ? 0.0 : dg_y / dg_d;
+    return 0.0;
+}
+
+// New direction with beta*ZA and the descent safeguard; returns g.d.
+__device__ bool direction(Ctx& C, int a, int c, bool initial, double& dmax, double& gd) {
+    double dots[8];
+    if (!ph_dir_dots(C, a, c, dots)) return false;
+    const double y_gn = dots[0], y_go = dots[1], dg_y = dots[2], dg_d = dots[3];
+    const double gn_d = dots[4], gn_gn = dots[5], gn_go = dots[6], dg_gn = dots[7];
+    int kind = 1;
+    double beta = 0.0;
+    if (initial) {
+        gd = -y_gn;
+        if (gd >= 0.0) {
+            kind = 3;
+            gd = -gn_gn;
+        }
+    } else {
+        beta = beta_za(y_gn, y_go, dg_y, dg_d);
+        gd = -y_gn + beta * gn_d;
+        if (gd >= 0.0) {
+            beta = beta_za(gn_gn, gn_go, dg_gn, dg_d);
+            kind = 2;
+            gd = -gn_gn + beta * gn_d;
+            if (gd >= 0.0) {
+                kind = 3;
+                beta = 0.0;
+                gd = -gn_gn;
+            }
+        }
+    }
+    return ph_dir_write(C, a, kind, beta, dmax);
+}
+
+__device__ __forceinline__ bool cubic_step(double f0, double g0, double a, double f1, double g1,
+                                           double& out) {
+    const double d1 = g0 + g1 - 3.0 * (f1 - f0) / a;
+    const double disc = d1 * d1 - g0 * g1;
+    if (!(disc > 0.0)) return false;
+    const double d2 = sqrt(disc);
+    const double den = g1 - g0 + 2.0 * d2;
+    if (den == 0.0) return false;
+    out = a - a * (g1 + d2 - d1) / den;
+    return isfinite(out);
+}
+
+// Algorithm 4 at the current field from slot C.cur.
+__device__ int minimize(Ctx& C, int& cur) {
+    const Problem& P = *C.P;
+    const Params& prm = P.prm;
+    int c = cur;
+    if (!evaluate(C, c, c, false, 0.0)) return ST_TIMEOUT;
+    if (!precond_solve(C, c)) return ST_TIMEOUT;
+    double dmax, gd;
+    if (!direction(C, c, c, true, dmax, gd)) return ST_TIMEOUT;
+    double a_prev = 1.0;
+    int status = ST_RUNNING;
+    if (!isfinite(C.sl[c].F)) status = ST_NONFINITE;
+    else if (C.sl[c].gmax == 0.0) status = ST_OK;
+    const double sq_tau = sqrt(prm.tau_F);
+    const double cb_tau = cbrt(prm.tau_F);
+    while (status == ST_RUNNING && C.nli < prm.max_iter) {
+        const double F0 = C.sl[c].F;
+        const double dphi0 = gd;
+        const double a_max = prm.theta_max / dmax;
+        const double a_t = fmin(a_prev, a_max);
+        const int ts = (c + 1) % MM_NSLOT, ss = (c + 2) % MM_NSLOT;
+        if (!evaluate(C, c, ts, true, a_t)) return ST_TIMEOUT;
+        double a_s;
+        if (!cubic_step(F0, dphi0, a_t, C.sl[ts].F, C.sl[ts].dphi, a_s))
+            a_s = (C.sl[ts].dphi < 0.0) ? 4.0 * a_t : 0.5 * a_t;
+        a_s = fmin(fmax(a_s, 0.1 * a_t), fmin(4.0 * a_t, a_max));
+        if (!evaluate(C, c, ss, true, a_s)) return ST_TIMEOUT;
+        int b;
+        double a_b;
+        if (C.sl[ss].F <= C.sl[ts].F) {
+            b = ss;
+            a_b = a_s;
+        } else {
+            b = ts;
+            a_b = a_t;
+        }
+        if (!(C.sl[b].F <= F0 + prm.c1 * a_b * dphi0)) {
+            bool found = false;
+            double a = 0.5 * fmin(a_t, a_s);
+            for (int k = 0; k < prm.max_backtrack; ++k) {
+                if (!evaluate(C, c, ts, true, a)) return ST_TIMEOUT;
+                C.ls_extra++;
+                if (C.sl[ts].F <= F0 + prm.c1 * a * dphi0) {
+                    b = ts;
+                    a_b = a;
+                    found = true;
+                    break;
+                }
+                a *= 0.5;
+            }
+            if (!found) {
+                status = ST_STALLED;
+                break;
+            }
+        }
+        C.nli++;
+        const SlotScalars& S = C.sl[b];
+        if (!isfinite(S.F)) {
+            status = ST_NONFINITE;
+            break;
+        }
+        const bool t1 = F0 - S.F < prm.tau_F * (1.0 + fabs(S.F));
+        const bool t2 = S.xdiff < sq_tau * (1.0 + S.xmax);
+        const bool t3 = S.gmax < cb_tau * (1.0 + fabs(S.F));
+        if (!precond_solve(C, b)) return ST_TIMEOUT;
+        if (!direction(C, b, c, false, dmax, gd)) return ST_TIMEOUT;
+        c = b;
+        a_prev = a_b;
+        if (t1 && t2 && t3) status = ST_OK;
+    }
+    if (status == ST_RUNNING) status = ST_NOT_CONVERGED;
+    cur = c;
+    return status;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(MM_BLOCK) k_solver(const __grid_constant__ Problem P) {
+    Ctx C;
+    C.P = &P;
+    C.t.nb = gridDim.x;
+    C.t.rank = blockIdx.x;
+    C.t.count = P.bar;
+    C.t.gen = P.bar + 32;
+    C.t.err = P.err;
+    C.t.part = P.partials;
+    C.t.epoch = 0;
+    C.t.dead = false;
+    C.evals = C.nli = C.li = C.mi = C.ls_extra = 0;
+    C.y_is_g = 0;
+    int cur = P.state->cur;
+    C.h[0] = P.state->h[0];
+    C.h[1] = P.state->h[1];
+    C.h[2] = P.state->h[2];
+    int status = ST_OK;
+    switch (P.mode) {
+        case MODE_MINIMIZE:
+            status = minimize(C, cur);
+            break;
+        case MODE_EVAL:
+            if (!evaluate(C, cur, cur, false, 0.0)) status = ST_TIMEOUT;
+            break;
+        case MODE_PRECOND:
+            if (!precond_solve(C, cur)) status = ST_TIMEOUT;
+            break;
+        case MODE_HESS: {
+            // input v in idir[0], output in ihd
+            double vHv;
+            if (!ph_hess(C, cur, P.idir[0], 1.0, P.idir[0], 0.0, nullptr, P.ihd, vHv)) status = ST_TIMEOUT;
+            break;
+        }
+        case MODE_KPHI: {
+            // input in pdir[0], output in pq
+            double vq;
+            if (!ph_pmatvec(C, P.pdir[0], P.pdir[0], 0.0, nullptr, P.pq, vq)) status = ST_TIMEOUT;
+            break;
+        }
+        default:
+            status = ST_TIMEOUT;
+    }
+    if (C.t.dead) status = ST_TIMEOUT;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        DevState* st = P.state;
+        st->cur = cur;
+        st->status = status;
+        st->evals = C.evals;
+        st->nli = C.nli;
+        st->li = C.li;
+        st->mi = C.mi;
+        st->ls_extra = C.ls_extra;
+        if (P.mode == MODE_MINIMIZE || P.mode == MODE_EVAL) {
+            const SlotScalars& S = C.sl[cur];
+            st->F = S.F;
+            for (int k = 0; k < 4; ++k) st->terms[k] = S.terms[k];
+            for (int k = 0; k < 3; ++k) st->M[k] = S.M[k];
+            st->gmax = S.gmax;
+        }
+        st->y_is_g = C.y_is_g;
+    }
+}
+
+}  // namespace mm

@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tolerances: operator applications (K_phi v, H v) 1e-12 relative; the
+energy 1e-10 relative and the gradient 1e-9 relative to its max norm against
+the exact (direct-solve) potential, with the GPU potential solved to a
+relative residual of 1e-13; minimisations: energy 1e-8 relative, max nodal
+|dm| 1e-5, coercive field 0.5%.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, energy, ncg, precond, curve
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(poisson_tol=1e-13)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_03690_gb300 import Magnet, Params
+    return Magnet, Params
+
+
+def _setup(lib, wl):
+    Magnet, Params = lib
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    P = fem.assemble_workload(wl)
+    return mag, P
+
+
+def _hard(n_mag=6, jitter=0.07, seed=4, box=2.0):
+    t = np.radians(25.0)
+    return synth.small_cube(n_mag=n_mag, h=1.5e-9, box_factor=box, Ms=1.28e6, A=7.7e-12,
+                            K1=4.3e6, axis=(np.sin(t), 0.2, np.cos(t)), jitter=jitter, seed=seed)
+
+
+def test_sizes_match_oracle(lib):
+    wl = _hard()
+    mag, P = _setup(lib, wl)
+    s = mag.sizes()
+    assert s["n_mag"] == P.n_mag
+    assert s["n_phi"] == P.n_phi
+    assert s["nnz_mag"] == P.KA.nnz
+    assert s["nnz_phi"] == P.Kphi.nnz
+
+
+@pytest.mark.parametrize("n_mag,box", [(6, 2.0), (5, 3.0)])
+def test_potential_matvec(lib, n_mag, box):
+    wl = _hard(n_mag=n_mag, box=box)
+    mag, P = _setup(lib, wl)
+    rng = np.random.default_rng(0)
+    v = rng.normal(size=wl.mesh.n_nodes)
+    out = mag.potential_matvec(v)
+    ref = np.zeros(wl.mesh.n_nodes)
+    ref[P.free_nodes] = P.Kphi @ v[P.free_nodes]
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-12 * scale)
+    assert np.all(out[P.dirichlet_nodes] == 0.0)
+
+
+def test_energy_terms_and_gradient(lib):
+    Magnet, Params = lib
+    wl = _hard()
+    mag, P = _setup(lib, wl)
+    b = np.array([0.3, -0.2, -1.5])
+    mag.set_field(b)
+    m = wl.m0
+    F, terms = mag.energy(m, Params(**TIGHT))
+    mo = energy.normalize(m[P.mag_nodes])
+    h = P.units.field_int(b)
+    e = energy.evaluate(P, mo, h)
+    EJ = P.units.energy_J
+    for k, name in enumerate(["exchange", "anisotropy", "demag", "zeeman"]):
+        assert terms[k] == pytest.approx(e["terms"][name] * EJ, rel=1e-10), name
+    assert F == pytest.approx(e["F"] * EJ, rel=1e-10)
+    g = mag.gradient(None, projected=False, params=Params(**TIGHT))
+    gp = mag.gradient(None, projected=True, params=Params(**TIGHT))
+    sc = np.abs(e["grad"]).max()
+    np.testing.assert_allclose(g[P.mag_nodes], e["grad"], rtol=0, atol=1e-9 * sc)
+    np.testing.assert_allclose(gp[P.mag_nodes], e["g"], rtol=0, atol=1e-9 * sc)
+    nonmag = np.setdiff1d(np.arange(wl.mesh.n_nodes), P.mag_nodes)
+    assert np.all(g[nonmag] == 0.0)
+    phi = mag.potential()
+    ref = np.zeros(wl.mesh.n_nodes)
+    ref[P.free_nodes] = e["phi"]
+    np.testing.assert_allclose(phi, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_potential_solve_matches_same_algorithm(lib):
+    """With equal tolerance and zero start the GPU potential solve and the
+    oracle's Algorithm 1 take the same steps."""
+    Magnet, Params = lib
+    wl = _hard(n_mag=5)
+    mag, P = _setup(lib, wl)
+    mo = energy.normalize(wl.m0[P.mag_nodes])
+    mag.set_magnetization(wl.m0)
+    F, terms = mag.energy(None, Params(poisson_tol=1e-8))
+    phi_or, steps = energy.solve_potential(P, mo, method="cg", tol=1e-8)
+    phi = mag.potential()[P.free_nodes]
+    np.testing.assert_allclose(phi, phi_or, rtol=0, atol=1e-11 * np.abs(phi_or).max())
+
+
+def test_hessian_apply(lib):
+    Magnet, Params = lib
+    for keep in (False, True):
+        wl = _hard()
+        mag, P = _setup(lib, wl)
+        mag.set_field([0.1, 0.0, 0.7])
+        grad = mag.gradient(wl.m0, projected=False, params=Params(**TIGHT))[P.mag_nodes]
+        rng = np.random.default_rng(1)
+        v = rng.normal(size=(wl.mesh.n_nodes, 3))
+        out = mag.hessian_apply(v, Params(keep_last_term=keep))[P.mag_nodes]
+        mo = energy.normalize(wl.m0[P.mag_nodes])
+        ref = precond.apply_H(P, mo, grad, v[P.mag_nodes], keep_last=keep)
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("jmax", [0, 1, 4, 12])
+def test_precond_solve(lib, jmax):
+    Magnet, Params = lib
+    wl = _hard()
+    mag, P = _setup(lib, wl)
+    mag.set_field([0.0, 0.0, 2.0])
+    grad = mag.gradient(wl.m0, projected=False, params=Params(**TIGHT))[P.mag_nodes]
+    mo = energy.normalize(wl.m0[P.mag_nodes])
+    g = energy.project(mo, grad)
+    y, steps = mag.precond_solve(Params(jmax=jmax))
+    y_or, steps_or = precond.precond_solve(P, mo, grad, g, jmax)
+    assert steps == steps_or
+    np.testing.assert_allclose(y[P.mag_nodes], y_or, rtol=0, atol=1e-10 * np.abs(y_or).max())
+
+
+@pytest.mark.parametrize("jmax", [0, 4])
+def test_minimize_parity_soft(lib, jmax):
+    Magnet, Params = lib
+    wl = synth.small_cube(n_mag=4, h=2e-9, jitter=0.05, seed=3)
+    mag, P = _setup(lib, wl)
+    b = np.array([0.02, 0.0, 0.05])
+    mag.set_magnetization(wl.m0)
+    mag.set_field(b)
+    st = mag.minimize(Params(jmax=jmax, **TIGHT))
+    m = mag.get_magnetization()[P.mag_nodes]
+    r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=jmax))
+    assert st["status"] == "ok" and r.status == "converged"
+    assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+    assert np.abs(m - r.m).max() < 1e-5
+    np.testing.assert_allclose(np.linalg.norm(m, axis=1), 1.0, atol=1e-14)
+    assert st["evals"] == 2 * st["nli"] + 1 + st["ls_extra"]
+    assert st["li"] <= jmax * (st["nli"] + 1)
+
+
+def test_coercive_field_parity(lib):
+    """A small hard-magnetic cube swept through switching: the GPU curve's
+    coercive field agrees with the oracle's within 0.5%."""
+    Magnet, Params = lib
+    t = np.radians(1.0)
+    wl = synth.small_cube(n_mag=3, h=1e-9, box_factor=2.0, Ms=1.28e6, A=7.7e-12, K1=4.3e6,
+                          axis=(np.sin(t), 0.0, np.cos(t)), m0=(0, 0, 1))
+    mag, P = _setup(lib, wl)
+    bz = -np.linspace(5.0, 7.0, 21)
+    fields = np.stack([np.zeros_like(bz), np.zeros_like(bz), bz], axis=1)
+    mag.set_magnetization(wl.m0)
+    sts = mag.demag_curve(fields, Params(jmax=4, **TIGHT))
+    M = np.array([s["M"] for s in sts])
+    hc_gpu = curve.coercive_field(fields, M)
+    res = curve.demag_curve(P, fields, wl.m0, ncg.Params(jmax=4))
+    assert hc_gpu is not None and res["Hc_T"] is not None
+    assert abs(hc_gpu - res["Hc_T"]) <= 0.005 * res["Hc_T"]
+    np.testing.assert_allclose(M, res["M"], atol=1e-5)
+
+
+def test_magnet_touching_outer_boundary(lib):
+    """No air box: magnetic nodes on the outer surface carry phi = 0."""
+    Magnet, Params = lib
+    wl = synth.small_cube(n_mag=4, h=2e-9, box_factor=1.0, jitter=0.0, seed=2)
+    mag, P = _setup(lib, wl)
+    b = np.array([0.0, 0.1, 0.0])
+    mag.set_field(b)
+    F, terms = mag.energy(wl.m0, Params(**TIGHT))
+    e = energy.evaluate(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b))
+    assert F == pytest.approx(e["F"] * P.units.energy_J, rel=1e-10)
+
+
+def test_invalid_inputs(lib):
+    Magnet, Params = lib
+    from paper_1801_03690_gb300 import MMError
+    wl = synth.small_cube(n_mag=2, h=1e-9)
+    mag = Magnet(device=0)
+    bad = wl.mesh.tets.copy()
+    bad[0, 0] = wl.mesh.n_nodes + 5
+    with pytest.raises(MMError) as ei:
+        mag.upload_mesh(wl.mesh.xyz, bad, wl.mesh.region, wl.materials)
+    assert ei.value.status == -2
+    flat = wl.mesh.xyz.copy()
+    t0 = wl.mesh.tets[0]
+    flat[t0[3]] = flat[t0[0]] + 0.5 * (flat[t0[1]] - flat[t0[0]])  # collapse a tet
+    with pytest.raises(MMError):
+        mag.upload_mesh(flat, wl.mesh.tets, wl.mesh.region, wl.materials)
+    mag.upload_workload(wl)
+    m = wl.m0.copy()
+    P = fem.assemble_workload(wl)
+    m[P.mag_nodes[0]] = np.nan
+    with pytest.raises(MMError):
+        mag.set_magnetization(m)
+    with pytest.raises(MMError):
+        mag.minimize(Params(tau_F=-1.0))
+    air = wl.materials.copy()
+    air[:, 0] = 0.0
+    with pytest.raises(MMError):
+        mag.upload_mesh(wl.mesh.xyz, wl.mesh.tets, wl.mesh.region, air)
