@@ -186,6 +186,32 @@ int mm_potential_matvec(mm_ctx* ctx, const double* v, double* out);
 int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields,
                    const mm_params* p, mm_stats* stats_out);
 
+/* Energy and gradient at m without any device allocation in the call.
+ * The paper has no counterpart; this entry point is for callers that cannot
+ * call cudaMalloc: a process whose device memory is handed in full to its
+ * own pool allocator or held to a fixed quota, or a latency-bound loop that
+ * cannot afford the device-wide synchronisation of cudaFree.  It runs the
+ * same potential solve and energy/gradient pass as mm_energy and
+ * mm_gradient, on the operators assembled by mm_upload_mesh (which did
+ * allocate, once), at the field of the last mm_set_field, with every work
+ * vector in one fixed 8 MiB device array of the library.  That array is
+ * held by every GPU that loads the library until the process exits.
+ *   m_dev      [n_nodes][3] doubles on the context's device (normalised here)
+ *   grad_dev   [n_nodes][3] output, or NULL; projected = 1 gives Pi grad F;
+ *              internal units as in mm_gradient; non-magnetic rows are 0
+ *   energy_dev 5 doubles output: F and the four terms of mm_energy, in J
+ * The potential solve starts from zero on every call.  Size limit:
+ * 11 n_mag + 6 n_phi doubles plus about 32 doubles per persistent block
+ * must fit in 8 MiB (about n_phi <= 150,000 for a cube in a box twice its
+ * size); larger problems return MM_ERR_ARG with the required size.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture.  Every call shares the array and leaves its
+ * contents behind; calls that overlap on the GPU (other contexts or threads
+ * on the same device) race on it.  Synchronises the context's stream. */
+int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, const mm_params* p,
+                               double* grad_dev, int projected, double* energy_dev);
+
 /* Device time (ms) of the last persistent-kernel launch, from CUDA events
  * on the context's stream; synchronises. */
 int mm_last_kernel_ms(mm_ctx* ctx, double* ms);

@@ -72,6 +72,8 @@ EXPORTS = {
     "mm_demag_curve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(mm_params),
                                  C.POINTER(mm_stats)]),
     "mm_last_kernel_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mm_energy_gradient_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mm_params),
+                                             C.c_void_p, C.c_int, C.c_void_p]),
     "mm_stream": (C.c_void_p, [C.c_void_p]),
 }
 

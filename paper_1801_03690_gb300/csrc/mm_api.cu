@@ -332,6 +332,30 @@ int copy_out3(mm_ctx* ctx, const double* dev_soa, double* host) {
 
 }  // namespace
 
+namespace mm {
+
+int ctx_view(mm_ctx* ctx, CtxView* out) {
+    if (!ctx || !out) return MM_ERR_ARG;
+    out->P = &ctx->P;
+    out->stream = (void*)ctx->stream;
+    out->device = ctx->device;
+    out->blocks = ctx->blocks;
+    out->n_nodes = ctx->n_nodes;
+    out->nm = ctx->nm;
+    out->nphi = ctx->nphi;
+    out->Mref = ctx->Mref;
+    for (int k = 0; k < 3; ++k) out->field_T[k] = ctx->field_T[k];
+    out->mag_nodes = ctx->d_mag_nodes;
+    out->node_of_phi = ctx->d_node_of_phi;
+    out->ident = ctx->d_ident;
+    out->has_mesh = ctx->has_mesh;
+    return MM_OK;
+}
+
+int ctx_fail(mm_ctx* ctx, int code, const char* msg) { return fail(ctx, code, "%s", msg); }
+
+}  // namespace mm
+
 extern "C" {
 
 void mm_default_params(mm_params* p) {

@@ -115,4 +115,26 @@ struct Problem {
     int mode;
 };
 
+// Read-only view of a context for entry points defined outside mm_api.cu.
+struct CtxView {
+    const Problem* P;
+    void* stream;                // cudaStream_t
+    int device;
+    int blocks;
+    long long n_nodes;
+    int nm, nphi;
+    double Mref;
+    double field_T[3];
+    const int* mag_nodes;        // device
+    const int* node_of_phi;      // device
+    const unsigned char* ident;  // device
+    bool has_mesh;
+};
+
+}  // namespace mm
+
+struct mm_ctx;
+namespace mm {
+__attribute__((visibility("hidden"))) int ctx_view(mm_ctx* ctx, CtxView* out);
+__attribute__((visibility("hidden"))) int ctx_fail(mm_ctx* ctx, int code, const char* msg);
 }  // namespace mm
