@@ -38,8 +38,10 @@ def workload(name):
         return synth.hard_cube()
     if name == "soft_cube":
         return synth.soft_cube()
+    if name == "medium":
+        return synth.hard_cube(n_mag=44)
     if name == "small":
-        return synth.hard_cube(n_mag=12, n_fields=40)
+        return synth.hard_cube(n_mag=12)
     raise ValueError(name)
 
 
@@ -58,8 +60,10 @@ def alg_bytes(st, sz):
     """Bytes one minimisation launch must move at ideal reuse (every array
     element read or written once per phase, neighbour gathers served from
     cache), from the launch's own counters:
-      potential step (mi)   12 nnz_phi + 96 n_phi   (SELL val+col; z, d_old, d, q;
-                                                      phi, d, r, q, diag^-1 -> phi, r, z)
+      potential step (mi)   FP64: 12 nnz_phi + 96 n_phi (SELL val+col; z gather,
+                            d, q read+write; phi, d, r, q, diag^-1 -> phi, r, z)
+                            precision form: FP32 steps 8 nnz_phi + 52 n_phi,
+                            FP64 refinements (mr) 12 nnz_phi + 60 n_phi
       evaluation (evals)    12 nnz_phi + 64 nnz_mag + 48 n_phi + 208 n_mag
                             (potential set-up incl. D m; energy/gradient pass)
       trial point (evals-1) 112 n_mag
@@ -69,11 +73,15 @@ def alg_bytes(st, sz):
     nphi, nm = sz["n_phi"], sz["n_mag"]
     nzp, nzm = sz["nnz_phi"], sz["nnz_mag"]
     per_pcg = 12 * nzp + 96 * nphi
+    per_pcg32 = 8 * nzp + 52 * nphi          # FP32 step: val+col 8 B/nnz; 13 FP32 vector passes
+    per_refine = 12 * nzp + 60 * nphi        # FP64 residual product + FP32 set-up
     per_eval = 12 * nzp + 64 * nzm + 48 * nphi + 208 * nm
     per_trial = 112 * nm
     per_inner = 12 * nzm + 352 * nm
     per_iter = 272 * nm
-    return (st["mi"] * per_pcg + st["evals"] * per_eval + max(st["evals"] - 1, 0) * per_trial
+    mr = st.get("mr", 0)
+    steps = (st["mi"] - mr) * per_pcg32 + mr * per_refine if mr else st["mi"] * per_pcg
+    return (steps + st["evals"] * per_eval + max(st["evals"] - 1, 0) * per_trial
             + st["li"] * per_inner + (st["nli"] + 1) * per_iter)
 
 
@@ -157,9 +165,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "soft_cube", "small"])
+    ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "medium", "soft_cube", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="solver kernel instantiation / grid (0 = default)")
     args = ap.parse_args()
     K, W = args.steps, max(args.warmup, 0)
 
@@ -191,11 +201,9 @@ def main():
 
     wl = workload(args.workload)
     fields = wl.fields
-    n_steps_needed = W + K
-    if n_steps_needed > len(fields):
+    if W + K > len(fields):
         raise SystemExit(f"--warmup + --steps must be <= {len(fields)} field steps")
-    prm = Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10)
-    mag = Magnet(device=local_rank)
+    mag = Magnet(device=local_rank, blocks_per_sm=args.blocks_per_sm)
     mag.upload_workload(wl)
     sz = mag.sizes()
     stream = torch.cuda.ExternalStream(mag.stream, device=torch.device("cuda", local_rank))
@@ -204,54 +212,65 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    # ---- device-resident run
-    mag.set_magnetization(wl.m0)
-    for k in range(W):
-        mag.set_field(fields[k])
-        mag.minimize(prm)
-    clocks = ClockSampler(local_rank)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    nli = 0
-    kern_ms = 0.0
-    bytes_total = 0
-    statuses = []
-    per_step = []
-    for k in range(W, W + K):
-        mag.set_field(fields[k])
-        mag.minimize_async(prm)
-        st = mag.get_stats()
-        ms = mag.last_kernel_ms()
-        kern_ms += ms
-        bytes_total += alg_bytes(st, sz)
-        nli += st["nli"]
-        statuses.append(st["status"])
-        per_step.append({"field_T": float(fields[k][2]), "nli": st["nli"], "evals": st["evals"],
-                         "mi": st["mi"], "li": st["li"], "Mz": st["M"][2], "ms": ms})
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ck = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    nli_all = nli
-    if world > 1:
+    def max_over_ranks(x):
+        if world == 1:
+            return x
         import torch.distributed as dist
-        t = torch.tensor([t_ms], device="cuda")
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        n = torch.tensor([nli], device="cuda", dtype=torch.float64)
-        dist.all_reduce(n)
-        nli_all = int(n.item())
-    value = nli_all / (t_max / 1000.0)
+        return float(t.item())
 
-    # ---- end to end through the public API with host buffers
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        return float(t.item())
+
+    def run_form(precision):
+        """W untimed field steps from m0, then K timed field steps."""
+        prm = Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=precision)
+        mag.set_magnetization(wl.m0)
+        for k in range(W):
+            mag.set_field(fields[k])
+            mag.minimize(prm)
+        clocks = ClockSampler(local_rank)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        nli, kern_ms, nbytes, per_step = 0, 0.0, 0, []
+        for k in range(W, W + K):
+            mag.set_field(fields[k])
+            mag.minimize_async(prm)
+            st = mag.get_stats()
+            ms = mag.last_kernel_ms()
+            kern_ms += ms
+            nbytes += alg_bytes(st, sz)
+            nli += st["nli"]
+            per_step.append({"field_T": float(fields[k][2]), "status": st["status"], "nli": st["nli"],
+                             "evals": st["evals"], "mi": st["mi"], "mr": st["mr"], "li": st["li"],
+                             "F_J": st["F"], "Mz": st["M"][2], "kernel_ms": ms})
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ck = clocks.stop()
+        t_ms = max_over_ranks(ev0.elapsed_time(ev1))
+        nli_all = sum_over_ranks(nli)
+        return {"prm": prm, "value": nli_all / (t_ms / 1000.0), "t_ms": t_ms, "nli": nli_all,
+                "kern_ms": kern_ms, "bytes": nbytes, "per_step": per_step, "clocks": ck,
+                "m": mag.get_magnetization(), "F": per_step[-1]["F_J"]}
+
+    fp64 = run_form(0)
+    x1 = run_form(1)
+
+    # ---- end to end through the public API with host buffers (precision form)
     e2e = None
     if not args.no_e2e:
+        prm = x1["prm"]
         m_host = torch.empty((wl.mesh.n_nodes, 3), dtype=torch.float64).pin_memory()
         m_host.copy_(torch.from_numpy(wl.m0))
         mag.set_magnetization(m_host.numpy())
@@ -271,10 +290,10 @@ def main():
             nli_e += st["nli"]
         torch.cuda.synchronize()
         barrier()
-        te = time.perf_counter() - t0
+        te = max_over_ranks(time.perf_counter() - t0)
         mbytes = wl.mesh.n_nodes * 3 * 8
-        e2e = {"value": nli_e / te, "unit": UNIT, "h2d_bytes_per_step": mbytes + 24,
-               "d2h_bytes_per_step": mbytes + 136}
+        e2e = {"value": sum_over_ranks(nli_e) / te, "unit": UNIT, "h2d_bytes_per_step": mbytes + 24,
+               "d2h_bytes_per_step": mbytes + 144, "form": "precision form (FP32 potential solve + FP64 refinement)"}
 
     if rank != 0:
         return 0
@@ -286,24 +305,35 @@ def main():
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    achieved = bytes_total / (kern_ms / 1000.0) / 1e9
+    achieved = x1["bytes"] / (x1["kern_ms"] / 1000.0) / 1e9
+    ach64 = fp64["bytes"] / (fp64["kern_ms"] / 1000.0) / 1e9
+    dm = float(np.abs(x1["m"] - fp64["m"]).max())
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": x1["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": x1["t_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32+fp64", "data": "synthetic",
         "config": workload_desc(args.workload, wl, sz),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "kernel": "k_solver",
-                     "peak_source": peak_src, "alg_bytes_per_launch": bytes_total / K,
-                     "kernel_ms_per_launch": kern_ms / K},
-        "demag_curve": {"form": "plain FP64", "fields_timed": K, "wall_s": t_max / 1000.0,
-                        "statuses": statuses, "per_step": per_step},
+                     "peak_source": peak_src, "alg_bytes_per_launch": x1["bytes"] / K,
+                     "kernel_ms_per_launch": x1["kern_ms"] / K},
+        "plain_fp64": {"value": fp64["value"], "unit": UNIT, "ms_per_step": fp64["t_ms"] / K,
+                       "dtype": "f64", "roofline_frac": ach64 / hbm, "achieved_gbs": ach64,
+                       "per_step": fp64["per_step"]},
+        "demag_curve": {"fields_timed": K, "wall_s_precision_form": x1["t_ms"] / 1000.0,
+                        "wall_s_plain_fp64": fp64["t_ms"] / 1000.0,
+                        "speedup_vs_plain_fp64": fp64["t_ms"] / x1["t_ms"],
+                        "final_energy_rel_diff": abs(x1["F"] - fp64["F"]) / abs(fp64["F"]),
+                        "final_max_abs_dm": dm, "per_step": x1["per_step"]},
         "gpu_launches": 2 * K,
     }
+    line["config"]["precision"] = "precision form: FP32 potential solve + FP64 refinement (plain FP64 in plain_fp64)"
     if e2e:
         line["e2e"] = e2e
-    if ck:
-        line["clocks"] = ck
+    if x1["clocks"]:
+        line["clocks"] = x1["clocks"]
+        if fp64["clocks"]:
+            line["clocks"]["reasons"] = sorted(set(x1["clocks"]["reasons"]) | set(fp64["clocks"]["reasons"]))
     if world == 1 and not args.no_cpu_baseline:
         nli_c, dt_c, desc = oracle_sample(wl, max_iter=1)
         line["cpu_baseline"] = {"value": nli_c / dt_c, "unit": UNIT, "cores": 1, "kind": "oracle",

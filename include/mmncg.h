@@ -84,6 +84,13 @@ typedef struct {
     int keep_last_term;    /* 1: keep the last term of Eq. (precond) (0)           */
     double poisson_tol;    /* relative residual of the potential solve (1e-10)     */
     int poisson_max_iter;  /* cap on potential-solve steps per evaluation (20000)  */
+    int precision;         /* 0: FP64 throughout (0); 1: precision form -- the    */
+                           /* potential solve runs Algorithm 1 in FP32 on the      */
+                           /* correction equation K delta = r and refines the      */
+                           /* residual r = D m - K phi in FP64 ("reliable          */
+                           /* updates") until poisson_tol                          */
+    double inner_tol;      /* FP32 residual drop that triggers an FP64 update (0.1)*/
+    int max_refine;        /* cap on FP64 updates per potential solve (64)         */
 } mm_params;
 
 /* Counters of one call, in the columns of Table 1 plus the energy. */
@@ -93,6 +100,7 @@ typedef struct {
     int64_t li;            /* products with H inside the preconditioner solves    */
     int64_t mi;            /* products with K_phi inside the potential solves     */
     int64_t ls_extra;      /* evaluations spent backtracking in the line search   */
+    int64_t mr;            /* FP64 refinement products (precision form; in mi)     */
     int32_t status;        /* MM_OK / MM_NOT_CONVERGED / MM_STALLED / error       */
     int32_t pad;
     double F;              /* energy at the returned state, J                     */
@@ -200,7 +208,8 @@ int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields,
  *   grad_dev   [n_nodes][3] output, or NULL; projected = 1 gives Pi grad F;
  *              internal units as in mm_gradient; non-magnetic rows are 0
  *   energy_dev 5 doubles output: F and the four terms of mm_energy, in J
- * The potential solve starts from zero on every call.  Size limit:
+ * The potential solve runs in FP64 (the precision field of p is ignored)
+ * and starts from zero on every call.  Size limit:
  * 11 n_mag + 6 n_phi doubles plus about 32 doubles per persistent block
  * must fit in 8 MiB (about n_phi <= 150,000 for a cube in a box twice its
  * size); larger problems return MM_ERR_ARG with the required size.  The

@@ -34,12 +34,13 @@ class mm_params(C.Structure):
     _fields_ = [("tau_F", C.c_double), ("jmax", C.c_int), ("max_iter", C.c_int),
                 ("theta_max", C.c_double), ("c1", C.c_double), ("max_backtrack", C.c_int),
                 ("keep_last_term", C.c_int), ("poisson_tol", C.c_double),
-                ("poisson_max_iter", C.c_int)]
+                ("poisson_max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
+                ("max_refine", C.c_int)]
 
 
 class mm_stats(C.Structure):
     _fields_ = [("evals", C.c_int64), ("nli", C.c_int64), ("li", C.c_int64), ("mi", C.c_int64),
-                ("ls_extra", C.c_int64), ("status", C.c_int32), ("pad", C.c_int32),
+                ("ls_extra", C.c_int64), ("mr", C.c_int64), ("status", C.c_int32), ("pad", C.c_int32),
                 ("F", C.c_double), ("terms", C.c_double * 4), ("F_internal", C.c_double),
                 ("M", C.c_double * 3)]
 

@@ -31,6 +31,9 @@ class Params:
     keep_last_term: bool = False
     poisson_tol: float = 1e-10
     poisson_max_iter: int = 20000
+    precision: int = 0           # 1 = FP32 potential solve with FP64 refinement
+    inner_tol: float = 0.1
+    max_refine: int = 64
 
     def to_c(self):
         p = L.mm_params()
@@ -41,7 +44,7 @@ class Params:
 
 
 def _stats_dict(s):
-    return {"evals": s.evals, "nli": s.nli, "li": s.li, "mi": s.mi, "ls_extra": s.ls_extra,
+    return {"evals": s.evals, "nli": s.nli, "li": s.li, "mi": s.mi, "ls_extra": s.ls_extra, "mr": s.mr,
             "status": L.STATUS_NAMES.get(s.status, s.status), "status_code": s.status,
             "F": s.F, "terms": list(s.terms), "F_internal": s.F_internal, "M": list(s.M)}
 

@@ -16,9 +16,6 @@
 #include "mm_assemble.cuh"
 #include "mm_internal.cuh"
 
-namespace mm {
-__global__ void k_solver(const __grid_constant__ Problem P);
-}
 
 namespace {
 
@@ -85,6 +82,11 @@ __global__ void k_set_field(mm::DevState* st, double h0, double h1, double h2) {
 
 __global__ void k_set_cur(mm::DevState* st, int cur) { st->cur = cur; }
 
+__global__ void k_to_f32(long long n, const double* a, float* b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 inline int nblk(long long n, int b = 256) { return (int)((n + b - 1) / b); }
 
 }  // namespace
@@ -96,6 +98,7 @@ struct mm_ctx {
     int nsm = 0;
     int blocks = 0;
     int blocks_per_sm_req = 0;
+    const void* kernel = nullptr;
     std::string err;
     // mesh
     bool has_mesh = false;
@@ -174,6 +177,9 @@ mm::Params to_params(const mm_params* p) {
     q.keep_last_term = p->keep_last_term;
     q.poisson_tol = p->poisson_tol;
     q.poisson_max_iter = p->poisson_max_iter;
+    q.precision = p->precision;
+    q.inner_tol = p->inner_tol;
+    q.max_refine = p->max_refine;
     return q;
 }
 
@@ -187,6 +193,10 @@ int check_params(mm_ctx* ctx, const mm_params* p) {
     if (p->max_backtrack < 0) return fail(ctx, MM_ERR_ARG, "max_backtrack must be >= 0");
     if (!(p->poisson_tol > 0.0)) return fail(ctx, MM_ERR_ARG, "poisson_tol must be > 0");
     if (p->poisson_max_iter < 1) return fail(ctx, MM_ERR_ARG, "poisson_max_iter must be >= 1");
+    if (p->precision != 0 && p->precision != 1) return fail(ctx, MM_ERR_ARG, "precision must be 0 or 1");
+    if (p->precision == 1 && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
+        return fail(ctx, MM_ERR_ARG, "inner_tol must be in (0, 1)");
+    if (p->precision == 1 && p->max_refine < 1) return fail(ctx, MM_ERR_ARG, "max_refine must be >= 1");
     return MM_OK;
 }
 
@@ -236,8 +246,7 @@ int launch_solver(mm_ctx* ctx, int mode, const mm::Params& prm) {
     CK_CUDA(cudaMemsetAsync(ctx->P.err, 0, sizeof(int), ctx->stream));
     void* args[] = {(void*)&ctx->P};
     CK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
-    CK_CUDA(cudaLaunchCooperativeKernel((const void*)mm::k_solver, dim3(ctx->blocks), dim3(MM_BLOCK), args, 0,
-                                        ctx->stream));
+    CK_CUDA(cudaLaunchCooperativeKernel(ctx->kernel, dim3(ctx->blocks), dim3(MM_BLOCK), args, 0, ctx->stream));
     CK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
     CK_CUDA(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(mm::DevState), cudaMemcpyDeviceToHost,
                             ctx->stream));
@@ -262,6 +271,7 @@ void fill_stats(mm_ctx* ctx, mm_stats* out) {
     out->li = s.li;
     out->mi = s.mi;
     out->ls_extra = s.ls_extra;
+    out->mr = s.mr;
     out->status = s.status;
     out->pad = 0;
     out->F = s.F * EJ;
@@ -349,6 +359,7 @@ int ctx_view(mm_ctx* ctx, CtxView* out) {
     out->node_of_phi = ctx->d_node_of_phi;
     out->ident = ctx->d_ident;
     out->has_mesh = ctx->has_mesh;
+    out->kernel = ctx->kernel;
     return MM_OK;
 }
 
@@ -369,6 +380,9 @@ void mm_default_params(mm_params* p) {
     p->keep_last_term = 0;
     p->poisson_tol = 1e-10;
     p->poisson_max_iter = 20000;
+    p->precision = 0;
+    p->inner_tol = 0.1;
+    p->max_refine = 64;
 }
 
 int mm_create(mm_ctx** out, const mm_options* opt) {
@@ -397,8 +411,12 @@ int mm_create(mm_ctx** out, const mm_options* opt) {
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
     if (!coop) return bail(MM_ERR_CUDA);
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    // blocks_per_sm selects the kernel instantiation (register budget) and
+    // the grid: 3 or 4 use the kernels bounded for that occupancy (0 = 4,
+    // the fastest measured on GB300), 1 or 2 the unbounded one.
+    ctx->kernel = mm::solver_kernel(ctx->blocks_per_sm_req > 0 ? ctx->blocks_per_sm_req : 4);
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mm::k_solver, MM_BLOCK, 0) != cudaSuccess || bps < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ctx->kernel, MM_BLOCK, 0) != cudaSuccess || bps < 1)
         return bail(MM_ERR_CUDA);
     if (ctx->blocks_per_sm_req > 0) bps = std::min(bps, ctx->blocks_per_sm_req);
     ctx->blocks = bps * ctx->nsm;
@@ -715,6 +733,23 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     if ((rc = dalloc(ctx, &P.pdir[0], nphi))) return rc;
     if ((rc = dalloc(ctx, &P.pdir[1], nphi))) return rc;
     if ((rc = dalloc(ctx, &P.pq, nphi))) return rc;
+    {
+        float *k32, *d32;
+        if ((rc = dalloc(ctx, &k32, nnzp))) return rc;
+        if ((rc = dalloc(ctx, &d32, nphi))) return rc;
+        k_to_f32<<<nblk(nnzp), 256, 0, ctx->stream>>>(nnzp, Kp, k32);
+        k_to_f32<<<nblk(nphi), 256, 0, ctx->stream>>>(nphi, dinvP, d32);
+        CK_CUDA(cudaGetLastError());
+        P.Kp32 = k32;
+        P.dinvP32 = d32;
+        if ((rc = dalloc(ctx, &P.pres32, nphi))) return rc;
+        if ((rc = dalloc(ctx, &P.pprec32, nphi))) return rc;
+        if ((rc = dalloc(ctx, &P.pdir32, nphi))) return rc;
+        if ((rc = dalloc(ctx, &P.pq32, nphi))) return rc;
+        if ((rc = dalloc(ctx, &P.pdelta32, nphi))) return rc;
+        for (float* f : {P.pres32, P.pprec32, P.pdir32, P.pq32, P.pdelta32})
+            CK_CUDA(cudaMemsetAsync(f, 0, nphi * sizeof(float), ctx->stream));
+    }
     if ((rc = dalloc(ctx, &P.partials, 2 * (size_t)MM_MAXRED * ctx->blocks))) return rc;
     if ((rc = dalloc(ctx, &P.bar, 64))) return rc;
     if ((rc = dalloc(ctx, &P.err, 1))) return rc;

@@ -48,13 +48,16 @@ struct Params {
     int keep_last_term;
     double poisson_tol;
     int poisson_max_iter;
+    int precision;           // 0 = FP64, 1 = FP32 potential solve + FP64 refinement
+    double inner_tol;        // FP32 solve: relative residual reduction per refinement
+    int max_refine;          // FP64 refinement steps per potential solve
 };
 
 // Scalars written back by the kernel (block 0) and read by the host.
 struct DevState {
     int cur;                 // index of the current slot
     int status;
-    long long evals, nli, li, mi, ls_extra;
+    long long evals, nli, li, mi, ls_extra, mr;
     double F;                // internal units
     double terms[4];         // exchange, anisotropy, demag, Zeeman (internal)
     double M[3];             // weighted mean magnetisation of the current slot
@@ -106,6 +109,14 @@ struct Problem {
     double* pprec;           // [nphi] Jacobi-preconditioned residual
     double* pdir[2];         // [nphi] direction (double buffer)
     double* pq;              // [nphi] K_phi * direction
+    // precision form: FP32 copies of K_phi and diag^-1, FP32 work vectors
+    const float* Kp32;
+    const float* dinvP32;
+    float* pres32;           // [nphi] residual of the correction equation
+    float* pprec32;
+    float* pdir32;
+    float* pq32;
+    float* pdelta32;         // [nphi] correction
     // team machinery
     double* partials;        // [2][MM_MAXRED][nblocks]
     unsigned* bar;           // [0] = arrival count, [32] = generation
@@ -129,12 +140,16 @@ struct CtxView {
     const int* node_of_phi;      // device
     const unsigned char* ident;  // device
     bool has_mesh;
+    const void* kernel;          // the solver kernel the context launches
 };
 
 }  // namespace mm
 
 struct mm_ctx;
 namespace mm {
+// Device function pointer of the solver kernel built for at least
+// min_blocks resident blocks per SM (1, 3 or 4).
+const void* solver_kernel(int min_blocks);
 __attribute__((visibility("hidden"))) int ctx_view(mm_ctx* ctx, CtxView* out);
 __attribute__((visibility("hidden"))) int ctx_fail(mm_ctx* ctx, int code, const char* msg);
 }  // namespace mm

@@ -24,10 +24,6 @@
 #include "../../include/mmncg.h"
 #include "mm_internal.cuh"
 
-namespace mm {
-__global__ void k_solver(const __grid_constant__ Problem P);
-}
-
 namespace {
 
 constexpr size_t kScratchDoubles = (size_t)1 << 20;   // 8 MiB
@@ -175,6 +171,10 @@ extern "C" int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, cons
     Q.prm.keep_last_term = p->keep_last_term;
     Q.prm.poisson_tol = p->poisson_tol;
     Q.prm.poisson_max_iter = p->poisson_max_iter;
+    Q.prm.precision = 0;                            // the FP64 evaluation only
+    Q.prm.inner_tol = p->inner_tol;
+    Q.prm.max_refine = p->max_refine;
+    Q.pres32 = Q.pprec32 = Q.pdir32 = Q.pq32 = Q.pdelta32 = nullptr;
 
     const double hs = 1.0 / (kMu0 * v.Mref);
     int* bad = (int*)(S + o_bad);
@@ -189,8 +189,7 @@ extern "C" int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, cons
                                                    v.field_T[1] * hs, v.field_T[2] * hs, bad);
     if ((e = cudaGetLastError()) != cudaSuccess) return mm::ctx_fail(ctx, MM_ERR_CUDA, cudaGetErrorString(e));
     void* args[] = {(void*)&Q};
-    if ((e = cudaLaunchCooperativeKernel((const void*)mm::k_solver, dim3(v.blocks), dim3(MM_BLOCK), args, 0, st)) !=
-        cudaSuccess)
+    if ((e = cudaLaunchCooperativeKernel(v.kernel, dim3(v.blocks), dim3(MM_BLOCK), args, 0, st)) != cudaSuccess)
         return mm::ctx_fail(ctx, MM_ERR_CUDA, cudaGetErrorString(e));
     if (grad_dev &&
         (e = cudaMemsetAsync(grad_dev, 0, (size_t)v.n_nodes * 3 * sizeof(double), st)) != cudaSuccess)

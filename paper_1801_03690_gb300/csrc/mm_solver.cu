@@ -163,7 +163,7 @@ struct SlotScalars {
 struct Ctx {
     const Problem* P;
     Team t;
-    long long evals, nli, li, mi, ls_extra;
+    long long evals, nli, li, mi, ls_extra, mr;
     double h[3];
     SlotScalars sl[MM_NSLOT];
     int y_is_g;
@@ -241,37 +241,47 @@ __device__ bool ph_pinit(Ctx& C, int s, double& bb, double& rz, double& rr) {
     return true;
 }
 
-// q = K v with v_j = A_j + beta * Bv_j formed on the fly (the new CG
-// direction); v_p is stored to vout.  Sum: v . q.
-__device__ bool ph_pmatvec(Ctx& C, const double* A, const double* Bv, double beta,
-                           double* vout, double* q, double& vq) {
+// Plain product q = K v (no reduction).
+__device__ bool ph_pmatvec(Ctx& C, const double* v, double* q) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    ROWS(p, P.nphi) {
+        Row rw = sell_row(P.p_sptr, p);
+        double s = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < rw.width; ++k) {
+            const long long e = rw.base + 32ll * k;
+            s += P.Kp[e] * v[P.p_col[e]];
+        }
+        q[p] = s;
+    }
+    return team_sync(t);
+}
+
+// CG direction step of Algorithm 1 with the product formed by recurrence:
+// w = K z, d = z + beta d, q = w + beta q (= K d), in place.  Sum: d . q.
+__device__ bool ph_pdirection(Ctx& C, const double* z, double beta, double* d, double* q, double& dq) {
     const Problem& P = *C.P;
     Team& t = C.t;
     double acc[1] = {0.0};
     double dummy[1] = {0.0};
-    const bool useB = (beta != 0.0);
+    const bool first = (beta == 0.0);
     ROWS(p, P.nphi) {
         Row rw = sell_row(P.p_sptr, p);
         double s = 0.0;
-        if (useB) {
-            for (int k = 0; k < rw.width; ++k) {
-                const long long e = rw.base + 32ll * k;
-                const int j = P.p_col[e];
-                s += P.Kp[e] * (A[j] + beta * Bv[j]);
-            }
-        } else {
-            for (int k = 0; k < rw.width; ++k) {
-                const long long e = rw.base + 32ll * k;
-                s += P.Kp[e] * A[P.p_col[e]];
-            }
+#pragma unroll 4
+        for (int k = 0; k < rw.width; ++k) {
+            const long long e = rw.base + 32ll * k;
+            s += P.Kp[e] * z[P.p_col[e]];
         }
-        const double vp = useB ? A[p] + beta * Bv[p] : A[p];
-        if (vout) vout[p] = vp;
-        q[p] = s;
-        acc[0] += vp * s;
+        const double dn = first ? z[p] : z[p] + beta * d[p];
+        const double qn = first ? s : s + beta * q[p];
+        d[p] = dn;
+        q[p] = qn;
+        acc[0] += dn * qn;
     }
     if (!team_reduce<1, 0>(t, acc, dummy)) return false;
-    vq = acc[0];
+    dq = acc[0];
     return true;
 }
 
@@ -306,25 +316,173 @@ __device__ bool ph_pzero(Ctx& C) {
     return team_sync(t);
 }
 
+// ---- precision form of the potential solve: the correction equation
+// K delta = r (r the FP64 residual) is solved by Algorithm 1 in FP32 (FP32
+// operator, vectors and products; FP64 reductions); then phi += delta and
+// r -= K delta in FP64 (iterative refinement of the FP64 residual).
+
+// r32 = r, z32 = diag^-1 r32, delta = 0.  Sums: r.z, |r|^2.
+__device__ bool ph_p32_init(Ctx& C, double& rz, double& rr) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    double acc[2] = {0.0, 0.0};
+    double dummy[1] = {0.0};
+    ROWS(p, P.nphi) {
+        const float r = (float)P.pres[p];
+        const float z = r * P.dinvP32[p];
+        P.pres32[p] = r;
+        P.pprec32[p] = z;
+        P.pdelta32[p] = 0.0f;
+        acc[0] += (double)r * (double)z;
+        acc[1] += (double)r * (double)r;
+    }
+    if (!team_reduce<2, 0>(t, acc, dummy)) return false;
+    rz = acc[0];
+    rr = acc[1];
+    return true;
+}
+
+// FP32 direction step: d = z + beta d, q = K32 z + beta q.  Sum: d . q.
+__device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    double acc[1] = {0.0};
+    double dummy[1] = {0.0};
+    const bool first = (beta == 0.0f);
+    const float* z = P.pprec32;
+    ROWS(p, P.nphi) {
+        Row rw = sell_row(P.p_sptr, p);
+        float s = 0.0f;
+#pragma unroll 4
+        for (int k = 0; k < rw.width; ++k) {
+            const long long e = rw.base + 32ll * k;
+            s += P.Kp32[e] * z[P.p_col[e]];
+        }
+        const float dn = first ? z[p] : z[p] + beta * P.pdir32[p];
+        const float qn = first ? s : s + beta * P.pq32[p];
+        P.pdir32[p] = dn;
+        P.pq32[p] = qn;
+        acc[0] += (double)dn * (double)qn;
+    }
+    if (!team_reduce<1, 0>(t, acc, dummy)) return false;
+    dq = acc[0];
+    return true;
+}
+
+// delta += a d; r -= a q; z = diag^-1 r.  Sums: r.z, |r|^2.
+__device__ bool ph_p32_update(Ctx& C, float a, double& rz, double& rr) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    double acc[2] = {0.0, 0.0};
+    double dummy[1] = {0.0};
+    ROWS(p, P.nphi) {
+        P.pdelta32[p] += a * P.pdir32[p];
+        const float r = P.pres32[p] - a * P.pq32[p];
+        const float z = r * P.dinvP32[p];
+        P.pres32[p] = r;
+        P.pprec32[p] = z;
+        acc[0] += (double)r * (double)z;
+        acc[1] += (double)r * (double)r;
+    }
+    if (!team_reduce<2, 0>(t, acc, dummy)) return false;
+    rz = acc[0];
+    rr = acc[1];
+    return true;
+}
+
+// FP64 refinement: phi += delta; r -= K delta (FP64 operator).  Sum: |r|^2.
+__device__ bool ph_p64_refine(Ctx& C, double& rr) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    double acc[1] = {0.0};
+    double dummy[1] = {0.0};
+    const float* dl = P.pdelta32;
+    ROWS(p, P.nphi) {
+        Row rw = sell_row(P.p_sptr, p);
+        double s = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < rw.width; ++k) {
+            const long long e = rw.base + 32ll * k;
+            s += P.Kp[e] * (double)dl[P.p_col[e]];
+        }
+        P.phi[p] += (double)dl[p];
+        const double r = P.pres[p] - s;
+        P.pres[p] = r;
+        acc[0] += r * r;
+    }
+    if (!team_reduce<1, 0>(t, acc, dummy)) return false;
+    rr = acc[0];
+    return true;
+}
+
+// Precision form of the potential solve: Algorithm 1 runs in FP32 on the
+// correction equation K delta = r and keeps its direction across
+// "reliable updates" (Clark et al., Comput. Phys. Commun. 181 (2010)):
+// whenever the FP32 residual has dropped by inner_tol relative to its
+// largest value since the last update (or below the target), the
+// correction is folded into phi in FP64, the FP64 residual is recomputed
+// from it (r -= K delta), and FP32 continues from that residual with the
+// same direction.  Stops when the FP64 residual meets poisson_tol.
+__device__ bool solve_potential_mixed(Ctx& C, double bb, double rr) {
+    const Problem& P = *C.P;
+    const double tol2 = P.prm.poisson_tol * P.prm.poisson_tol * bb;
+    const double upd2 = P.prm.inner_tol * P.prm.inner_tol;
+    if (rr < tol2) return true;
+    double rz, r32;
+    if (!ph_p32_init(C, rz, r32)) return false;
+    double rmax = r32;
+    float beta = 0.0f;
+    long long k = 0;
+    int updates = 0;
+    while (k < P.prm.poisson_max_iter) {
+        double dq;
+        if (!ph_p32_direction(C, beta, dq)) return false;
+        const float a = (float)(rz / dq);
+        double rzn;
+        if (!ph_p32_update(C, a, rzn, r32)) return false;
+        ++k;
+        if (r32 < upd2 * rmax || r32 < tol2) {
+            // reliable update
+            if (!ph_p64_refine(C, rr)) return false;
+            C.mr++;
+            ++updates;
+            if (rr < tol2 || updates >= P.prm.max_refine) {
+                C.mi += k + updates;
+                return true;
+            }
+            if (!ph_p32_init(C, rzn, r32)) return false;
+            rmax = r32;
+        } else {
+            rmax = fmax(rmax, r32);
+        }
+        beta = (float)(rzn / rz);
+        rz = rzn;
+    }
+    // iteration cap: fold the pending correction into phi
+    if (!ph_p64_refine(C, rr)) return false;
+    C.mr++;
+    C.mi += k + updates + 1;
+    return true;
+}
+
 // Algorithm 1 on K_phi phi = D m (Sec. 3.1), warm-started from phi.
 __device__ bool solve_potential(Ctx& C, int s) {
     const Problem& P = *C.P;
     double bb, rz, rr;
     if (!ph_pinit(C, s, bb, rz, rr)) return false;
     if (bb == 0.0) return ph_pzero(C);
+    if (P.prm.precision == 1) return solve_potential_mixed(C, bb, rr);
     const double tol2 = P.prm.poisson_tol * P.prm.poisson_tol * bb;
     double beta = 0.0;
-    int cb = 0;
     long long k = 0;
     while (rr >= tol2 && k < P.prm.poisson_max_iter) {
         double pq;
-        if (!ph_pmatvec(C, P.pprec, P.pdir[cb], beta, P.pdir[1 - cb], P.pq, pq)) return false;
+        if (!ph_pdirection(C, P.pprec, beta, P.pdir[0], P.pq, pq)) return false;
         const double a = rz / pq;
         double rzn;
-        if (!ph_pupdate(C, P.pdir[1 - cb], a, rzn, rr)) return false;
+        if (!ph_pupdate(C, P.pdir[0], a, rzn, rr)) return false;
         beta = rzn / rz;
         rz = rzn;
-        cb = 1 - cb;
         ++k;
     }
     C.mi += k;
@@ -420,44 +578,35 @@ __device__ bool evaluate(Ctx& C, int c, int s, bool trial, double a) {
     return true;
 }
 
-// out = H(m) v with v_i = ca*A_i + cb*Bv_i formed on the fly (Eq. precond,
-// magnetostatics dropped; last term only if keep_last_term); v is stored to
-// vout if given.  Sum: v . Hv.
-__device__ bool ph_hess(Ctx& C, int s, const double* A, double ca, const double* Bv, double cb,
-                        double* vout, double* out, double& vHv) {
+// w = H(m) v (Eq. precond, magnetostatics dropped; last term only if
+// keep_last_term).  With d given, the inner CG direction step follows by
+// recurrence: d = ca v + beta d and hd = ca w + beta hd (= H d), in place,
+// sum d . hd.  Without d, w is written to hd (sum v . w).
+__device__ bool ph_hess(Ctx& C, int s, const double* v, double ca, double beta, double* d,
+                        double* hd, double& dHd) {
     const Problem& P = *C.P;
     Team& t = C.t;
     const int nm = P.nm;
     const double* m = P.X[s];
     const double* lamv = P.LAM[s];
     const double* gr = P.GR[s];
-    const bool useB = (cb != 0.0);
     const bool keep = P.prm.keep_last_term != 0;
+    const bool first = (beta == 0.0);
     double acc[1] = {0.0};
     double dummy[1] = {0.0};
     ROWS(i, nm) {
         Row rw = sell_row(P.m_sptr, i);
         double c0 = 0, c1 = 0, c2 = 0;
+#pragma unroll 4
         for (int k = 0; k < rw.width; ++k) {
             const long long e = rw.base + 32ll * k;
             const int j = P.m_col[e];
             const double ka = P.KA[e];
-            double v0 = ca * A[j], v1 = ca * A[nm + j], v2 = ca * A[2 * nm + j];
-            if (useB) {
-                v0 += cb * Bv[j];
-                v1 += cb * Bv[nm + j];
-                v2 += cb * Bv[2 * nm + j];
-            }
-            c0 += ka * v0;
-            c1 += ka * v1;
-            c2 += ka * v2;
+            c0 += ka * v[j];
+            c1 += ka * v[nm + j];
+            c2 += ka * v[2 * nm + j];
         }
-        double v0 = ca * A[i], v1 = ca * A[nm + i], v2 = ca * A[2 * nm + i];
-        if (useB) {
-            v0 += cb * Bv[i];
-            v1 += cb * Bv[nm + i];
-            v2 += cb * Bv[2 * nm + i];
-        }
+        const double v0 = v[i], v1 = v[nm + i], v2 = v[2 * nm + i];
         const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
         const double kyy = P.CK[3 * nm + i], kyz = P.CK[4 * nm + i], kzz = P.CK[5 * nm + i];
         const double Cv0 = 2.0 * c0 + (kxx * v0 + kxy * v1 + kxz * v2);
@@ -466,27 +615,40 @@ __device__ bool ph_hess(Ctx& C, int s, const double* A, double ca, const double*
         const double m0 = m[i], m1 = m[nm + i], m2 = m[2 * nm + i];
         const double mc = m0 * Cv0 + m1 * Cv1 + m2 * Cv2;
         const double lam = lamv[i];
-        double h0 = Cv0 - mc * m0 - lam * v0;
-        double h1 = Cv1 - mc * m1 - lam * v1;
-        double h2 = Cv2 - mc * m2 - lam * v2;
+        double w0 = Cv0 - mc * m0 - lam * v0;
+        double w1 = Cv1 - mc * m1 - lam * v1;
+        double w2 = Cv2 - mc * m2 - lam * v2;
         if (keep) {
             const double vg = v0 * gr[i] + v1 * gr[nm + i] + v2 * gr[2 * nm + i];
-            h0 -= vg * m0;
-            h1 -= vg * m1;
-            h2 -= vg * m2;
+            w0 -= vg * m0;
+            w1 -= vg * m1;
+            w2 -= vg * m2;
         }
-        if (vout) {
-            vout[i] = v0;
-            vout[nm + i] = v1;
-            vout[2 * nm + i] = v2;
+        if (d) {
+            double dn[3] = {ca * v0, ca * v1, ca * v2};
+            double hn[3] = {ca * w0, ca * w1, ca * w2};
+            if (!first) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dn[c] += beta * d[c * nm + i];
+                    hn[c] += beta * hd[c * nm + i];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                d[c * nm + i] = dn[c];
+                hd[c * nm + i] = hn[c];
+                acc[0] += dn[c] * hn[c];
+            }
+        } else {
+            hd[i] = w0;
+            hd[nm + i] = w1;
+            hd[2 * nm + i] = w2;
+            acc[0] += v0 * w0 + v1 * w1 + v2 * w2;
         }
-        out[i] = h0;
-        out[nm + i] = h1;
-        out[2 * nm + i] = h2;
-        acc[0] += v0 * h0 + v1 * h1 + v2 * h2;
     }
     if (!team_reduce<1, 0>(t, acc, dummy)) return false;
-    vHv = acc[0];
+    dHd = acc[0];
     return true;
 }
 
@@ -524,12 +686,11 @@ __device__ bool precond_solve(Ctx& C, int s) {
     C.y_is_g = 0;
     if (ng < eps) return true;                  // y = 0 (only when g = 0 ... eps = 0)
     double beta = 0.0;
-    int cb = 0;
     int steps = 0;
     while (steps < jmax) {
         double dHd;
-        // direction d = -yv + beta d_old, formed on the fly and stored
-        if (!ph_hess(C, s, P.iprec, -1.0, P.idir[cb], beta, P.idir[1 - cb], P.ihd, dHd)) return false;
+        // direction d = -yv + beta d and H d, by recurrence
+        if (!ph_hess(C, s, P.iprec, -1.0, beta, P.idir[0], P.ihd, dHd)) return false;
         ++steps;
         C.li++;
         if (dHd <= 0.0) {                       // li2
@@ -537,7 +698,7 @@ __device__ bool precond_solve(Ctx& C, int s) {
             return true;
         }
         const double a = gy / dHd;
-        const double* dv = P.idir[1 - cb];
+        const double* dv = P.idir[0];
         double a2[2] = {0.0, 0.0};
         ROWS(i, nm) {
             const double di = P.dinvA[i];
@@ -557,7 +718,6 @@ __device__ bool precond_solve(Ctx& C, int s) {
         if (sqrt(a2[1]) < eps) return true;     // li3
         beta = a2[0] / gy;
         gy = a2[0];
-        cb = 1 - cb;
     }
     return true;                                // li1
 }
@@ -744,7 +904,7 @@ __device__ int minimize(Ctx& C, int& cur) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(MM_BLOCK) k_solver(const __grid_constant__ Problem P) {
+__device__ __forceinline__ void solver_body(const Problem& P) {
     Ctx C;
     C.P = &P;
     C.t.nb = gridDim.x;
@@ -755,7 +915,7 @@ __global__ void __launch_bounds__(MM_BLOCK) k_solver(const __grid_constant__ Pro
     C.t.part = P.partials;
     C.t.epoch = 0;
     C.t.dead = false;
-    C.evals = C.nli = C.li = C.mi = C.ls_extra = 0;
+    C.evals = C.nli = C.li = C.mi = C.ls_extra = C.mr = 0;
     C.y_is_g = 0;
     int cur = P.state->cur;
     C.h[0] = P.state->h[0];
@@ -775,13 +935,12 @@ __global__ void __launch_bounds__(MM_BLOCK) k_solver(const __grid_constant__ Pro
         case MODE_HESS: {
             // input v in idir[0], output in ihd
             double vHv;
-            if (!ph_hess(C, cur, P.idir[0], 1.0, P.idir[0], 0.0, nullptr, P.ihd, vHv)) status = ST_TIMEOUT;
+            if (!ph_hess(C, cur, P.idir[0], 1.0, 0.0, nullptr, P.ihd, vHv)) status = ST_TIMEOUT;
             break;
         }
         case MODE_KPHI: {
             // input in pdir[0], output in pq
-            double vq;
-            if (!ph_pmatvec(C, P.pdir[0], P.pdir[0], 0.0, nullptr, P.pq, vq)) status = ST_TIMEOUT;
+            if (!ph_pmatvec(C, P.pdir[0], P.pq)) status = ST_TIMEOUT;
             break;
         }
         default:
@@ -797,6 +956,7 @@ __global__ void __launch_bounds__(MM_BLOCK) k_solver(const __grid_constant__ Pro
         st->li = C.li;
         st->mi = C.mi;
         st->ls_extra = C.ls_extra;
+        st->mr = C.mr;
         if (P.mode == MODE_MINIMIZE || P.mode == MODE_EVAL) {
             const SlotScalars& S = C.sl[cur];
             st->F = S.F;
@@ -805,6 +965,21 @@ __global__ void __launch_bounds__(MM_BLOCK) k_solver(const __grid_constant__ Pro
             st->gmax = S.gmax;
         }
         st->y_is_g = C.y_is_g;
+    }
+}
+
+// One instantiation per occupancy target (minimum resident blocks per SM);
+// the host picks one (mm_options.blocks_per_sm, default 0 = no bound).
+template <int MINB>
+__global__ void __launch_bounds__(MM_BLOCK, MINB) k_solver(const __grid_constant__ Problem P) {
+    solver_body(P);
+}
+
+const void* solver_kernel(int min_blocks) {
+    switch (min_blocks) {
+        case 3: return (const void*)k_solver<3>;
+        case 4: return (const void*)k_solver<4>;
+        default: return (const void*)k_solver<1>;
     }
 }
 

@@ -1,0 +1,96 @@
+"""The precision form (FP32 potential solve with FP64 residual refinement)
+against the FP64 oracle.  Stated errors: energy 1e-10 relative at a potential
+tolerance of 1e-12; minimisation energy 1e-8 relative and max nodal |dm|
+1e-5; coercive field 0.5%."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, energy, ncg, curve
+
+pytestmark = pytest.mark.gpu
+
+
+def _hard(n_mag=6, seed=4, box=2.0):
+    t = np.radians(25.0)
+    return synth.small_cube(n_mag=n_mag, h=1.5e-9, box_factor=box, Ms=1.28e6, A=7.7e-12,
+                            K1=4.3e6, axis=(np.sin(t), 0.2, np.cos(t)), jitter=0.07, seed=seed)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_03690_gb300 import Magnet, Params
+    return Magnet, Params
+
+
+def test_precision_form_energy_and_gradient(lib):
+    Magnet, Params = lib
+    wl = _hard()
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    P = fem.assemble_workload(wl)
+    b = np.array([0.3, -0.2, -1.5])
+    mag.set_field(b)
+    prm = Params(precision=1, poisson_tol=1e-12)
+    F, terms = mag.energy(wl.m0, prm)
+    e = energy.evaluate(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b))
+    assert F == pytest.approx(e["F"] * P.units.energy_J, rel=1e-10)
+    g = mag.gradient(None, projected=True, params=prm)
+    np.testing.assert_allclose(g[P.mag_nodes], e["g"], rtol=0, atol=1e-9 * np.abs(e["grad"]).max())
+
+
+@pytest.mark.parametrize("jmax", [0, 4])
+def test_precision_form_minimize(lib, jmax):
+    Magnet, Params = lib
+    wl = synth.small_cube(n_mag=4, h=2e-9, jitter=0.05, seed=3)
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    P = fem.assemble_workload(wl)
+    b = np.array([0.02, 0.0, 0.05])
+    mag.set_magnetization(wl.m0)
+    mag.set_field(b)
+    st = mag.minimize(Params(jmax=jmax, precision=1, poisson_tol=1e-12))
+    m = mag.get_magnetization()[P.mag_nodes]
+    r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=jmax))
+    assert st["status"] == "ok" and r.status == "converged"
+    assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+    assert np.abs(m - r.m).max() < 1e-5
+    assert st["mr"] >= st["evals"]
+
+
+def test_precision_form_coercive_field(lib):
+    Magnet, Params = lib
+    t = np.radians(1.0)
+    wl = synth.small_cube(n_mag=3, h=1e-9, box_factor=2.0, Ms=1.28e6, A=7.7e-12, K1=4.3e6,
+                          axis=(np.sin(t), 0.0, np.cos(t)), m0=(0, 0, 1))
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    P = fem.assemble_workload(wl)
+    bz = -np.linspace(5.0, 7.0, 21)
+    fields = np.stack([np.zeros_like(bz), np.zeros_like(bz), bz], axis=1)
+    mag.set_magnetization(wl.m0)
+    sts = mag.demag_curve(fields, Params(jmax=4, precision=1))
+    hc = curve.coercive_field(fields, np.array([s["M"] for s in sts]))
+    res = curve.demag_curve(P, fields, wl.m0, ncg.Params(jmax=4))
+    assert abs(hc - res["Hc_T"]) <= 0.005 * res["Hc_T"]
+
+
+def test_precision_form_matches_fp64_form_on_a_jittered_cube(lib):
+    """Both GPU forms from the same start at the same field reach the same
+    minimum (energy 1e-8, m 1e-5)."""
+    Magnet, Params = lib
+    wl = synth.hard_cube(n_mag=10, jitter=0.07, seed=2)
+    out = []
+    for prec in (0, 1):
+        mag = Magnet(device=0)
+        mag.upload_workload(wl)
+        mag.set_magnetization(wl.m0)
+        mag.set_field([0.0, 0.0, -2.0])
+        st = mag.minimize(Params(precision=prec))
+        out.append((st, mag.get_magnetization()))
+        mag.close()
+    (s0, m0), (s1, m1) = out
+    assert s0["status"] == "ok" and s1["status"] == "ok"
+    assert s1["F"] == pytest.approx(s0["F"], rel=1e-8)
+    assert np.abs(m1 - m0).max() < 1e-5
