@@ -412,9 +412,9 @@ int mm_create(mm_ctx** out, const mm_options* opt) {
     if (!coop) return bail(MM_ERR_CUDA);
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     // blocks_per_sm selects the kernel instantiation (register budget) and
-    // the grid: 3 or 4 use the kernels bounded for that occupancy (0 = 4,
-    // the fastest measured on GB300), 1 or 2 the unbounded one.
-    ctx->kernel = mm::solver_kernel(ctx->blocks_per_sm_req > 0 ? ctx->blocks_per_sm_req : 4);
+    // the grid: 2, 3, 4 or 6 use the kernels bounded for that occupancy
+    // (0 = 3, the fastest measured on GB300), others the unbounded one.
+    ctx->kernel = mm::solver_kernel(ctx->blocks_per_sm_req > 0 ? ctx->blocks_per_sm_req : 3);
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ctx->kernel, MM_BLOCK, 0) != cudaSuccess || bps < 1)
         return bail(MM_ERR_CUDA);

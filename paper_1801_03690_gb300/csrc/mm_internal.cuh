@@ -148,7 +148,7 @@ struct CtxView {
 struct mm_ctx;
 namespace mm {
 // Device function pointer of the solver kernel built for at least
-// min_blocks resident blocks per SM (1, 3 or 4).
+// min_blocks resident blocks per SM (1, 2, 3, 4 or 6; others -> 1).
 const void* solver_kernel(int min_blocks);
 __attribute__((visibility("hidden"))) int ctx_view(mm_ctx* ctx, CtxView* out);
 __attribute__((visibility("hidden"))) int ctx_fail(mm_ctx* ctx, int code, const char* msg);

