@@ -69,7 +69,7 @@ typedef struct {
 
 typedef struct {
     int device;           /* CUDA device ordinal                                 */
-    int blocks_per_sm;    /* persistent-kernel blocks per SM; 0 = occupancy max  */
+    int blocks_per_sm;    /* solver kernel built for 2, 3 or 4 blocks/SM (0 = 3) */
     void* stream;         /* cudaStream_t to run on; NULL = a private stream     */
 } mm_options;
 
@@ -220,6 +220,43 @@ int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields,
  * on the same device) race on it.  Synchronises the context's stream. */
 int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, const mm_params* p,
                                double* grad_dev, int projected, double* energy_dev);
+
+/* ---- Batched minimisation (no counterpart in the paper: many independent
+ * magnets, e.g. sensor elements of different shapes, solved together).
+ * A batch groups contexts on one device, each with an uploaded mesh.  One
+ * cooperative launch runs Algorithm 4 for every member, each on its own team
+ * of blocks (teams synchronise only internally, so members of different
+ * sizes and iteration counts proceed independently).  Members keep their
+ * own state (m, potential, field); after a batch call the member contexts
+ * can be read with mm_get_magnetization etc.  At most as many members as
+ * co-resident blocks (about 3 x the SM count). */
+typedef struct mm_batch mm_batch;
+
+/* Split total_blocks over n teams in proportion to work[t]^gamma, at least
+ * one block each (largest-remainder rounding).  Pure host function. */
+int mm_batch_plan(int n, const int64_t* work, int total_blocks, double gamma,
+                  int32_t* blocks_out);
+int mm_batch_create(mm_batch** b, int n, mm_ctx* const* ctxs);
+void mm_batch_destroy(mm_batch* b);
+const char* mm_batch_last_error(const mm_batch* b);
+/* Kernel instantiation (3 or 4 blocks per SM) and team-split exponent. */
+int mm_batch_config(mm_batch* b, int blocks_per_sm, double gamma);
+/* Minimise every member at its current field from its current m (one
+ * launch); stats_out [n] (may be NULL).  Returns the first non-OK status. */
+int mm_batch_minimize(mm_batch* b, const mm_params* p, mm_stats* stats_out);
+/* Demagnetisation curves of every member: fields [n_steps][n][3] (mu0*H, T).
+ * One field step (set the fields, solve every member, record the stats) is
+ * captured once as a CUDA graph and replayed n_steps times with no host
+ * round trip in between.  stats_out [n_steps][n] (may be NULL). */
+int mm_batch_demag_curve(mm_batch* b, int64_t n_steps, const double* fields,
+                         const mm_params* p, mm_stats* stats_out);
+/* Time each kernel instantiation x team-split exponent on a short
+ * minimisation (max_iter capped at 25) of the members' current states,
+ * restoring the states after each trial, and keep the fastest. */
+int mm_batch_autotune(mm_batch* b, const mm_params* p, int* chosen_blocks_per_sm,
+                      double* chosen_gamma, double* best_ms);
+/* Device time (ms) of the last batch launch or curve. */
+int mm_batch_last_ms(mm_batch* b, double* ms);
 
 /* Device time (ms) of the last persistent-kernel launch, from CUDA events
  * on the context's stream; synchronises. */

@@ -73,6 +73,18 @@ EXPORTS = {
     "mm_demag_curve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(mm_params),
                                  C.POINTER(mm_stats)]),
     "mm_last_kernel_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mm_batch_plan": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_double,
+                                C.POINTER(C.c_int32)]),
+    "mm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
+    "mm_batch_destroy": (None, [C.c_void_p]),
+    "mm_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "mm_batch_config": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "mm_batch_minimize": (C.c_int, [C.c_void_p, C.POINTER(mm_params), C.POINTER(mm_stats)]),
+    "mm_batch_demag_curve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(mm_params),
+                                       C.POINTER(mm_stats)]),
+    "mm_batch_autotune": (C.c_int, [C.c_void_p, C.POINTER(mm_params), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mm_batch_last_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mm_energy_gradient_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mm_params),
                                              C.c_void_p, C.c_int, C.c_void_p]),
     "mm_stream": (C.c_void_p, [C.c_void_p]),

@@ -213,3 +213,79 @@ class Magnet:
         ms = C.c_double()
         self._check(self._lib.mm_last_kernel_ms(self._h, C.byref(ms)))
         return ms.value
+
+
+def batch_plan(work, total_blocks, gamma=1.0):
+    """Team sizes for a batch (pure host computation, no GPU needed)."""
+    lib = L.load()
+    w = np.ascontiguousarray(work, dtype=np.int64)
+    out = np.zeros(len(w), dtype=np.int32)
+    rc = lib.mm_batch_plan(len(w), w.ctypes.data_as(C.POINTER(C.c_int64)), int(total_blocks),
+                           float(gamma), out.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc != 0:
+        raise MMError(rc, "mm_batch_plan rejected its arguments")
+    return out
+
+
+class Batch:
+    """Many independent magnets minimised in one persistent launch."""
+
+    def __init__(self, magnets):
+        self._lib = L.load()
+        self.magnets = list(magnets)
+        arr = (C.c_void_p * len(self.magnets))(*[m._h.value for m in self.magnets])
+        h = C.c_void_p()
+        rc = self._lib.mm_batch_create(C.byref(h), len(self.magnets), arr)
+        if rc != 0:
+            raise MMError(rc, "mm_batch_create failed (every member needs a mesh, one device)")
+        self._h = h
+
+    def _check(self, rc, soft_ok=False):
+        if rc < 0 or (rc > 0 and not soft_ok):
+            raise MMError(rc, self._lib.mm_batch_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def config(self, blocks_per_sm=3, gamma=1.0):
+        self._check(self._lib.mm_batch_config(self._h, int(blocks_per_sm), float(gamma)))
+
+    def minimize(self, params=None):
+        p = (params or Params()).to_c()
+        st = (L.mm_stats * len(self.magnets))()
+        self._check(self._lib.mm_batch_minimize(self._h, C.byref(p), st), soft_ok=True)
+        return [_stats_dict(s) for s in st]
+
+    def demag_curve(self, fields, params=None):
+        """fields: [n_steps, n_members, 3] mu0*H in tesla."""
+        f = _f64(fields)
+        n = len(self.magnets)
+        f = f.reshape(-1, n, 3)
+        p = (params or Params()).to_c()
+        st = (L.mm_stats * (f.shape[0] * n))()
+        self._check(self._lib.mm_batch_demag_curve(self._h, f.shape[0], _ptr(f), C.byref(p), st),
+                    soft_ok=True)
+        return [[_stats_dict(st[s * n + t]) for t in range(n)] for s in range(f.shape[0])]
+
+    def autotune(self, params=None):
+        p = (params or Params()).to_c()
+        bps = C.c_int()
+        gamma = C.c_double()
+        ms = C.c_double()
+        self._check(self._lib.mm_batch_autotune(self._h, C.byref(p), C.byref(bps), C.byref(gamma),
+                                                C.byref(ms)))
+        return bps.value, gamma.value, ms.value
+
+    def last_ms(self):
+        ms = C.c_double()
+        self._check(self._lib.mm_batch_last_ms(self._h, C.byref(ms)))
+        return ms.value

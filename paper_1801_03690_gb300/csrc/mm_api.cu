@@ -344,6 +344,24 @@ int copy_out3(mm_ctx* ctx, const double* dev_soa, double* host) {
 
 namespace mm {
 
+const void* solver_kernel_2();
+const void* solver_kernel_3();
+const void* solver_kernel_4();
+const void* solver_batch_kernel_3();
+const void* solver_batch_kernel_4();
+
+const void* solver_kernel(int min_blocks) {
+    switch (min_blocks) {
+        case 2: return solver_kernel_2();
+        case 4: return solver_kernel_4();
+        default: return solver_kernel_3();
+    }
+}
+
+const void* solver_batch_kernel(int min_blocks) {
+    return min_blocks == 4 ? solver_batch_kernel_4() : solver_batch_kernel_3();
+}
+
 int ctx_view(mm_ctx* ctx, CtxView* out) {
     if (!ctx || !out) return MM_ERR_ARG;
     out->P = &ctx->P;
@@ -360,10 +378,21 @@ int ctx_view(mm_ctx* ctx, CtxView* out) {
     out->ident = ctx->d_ident;
     out->has_mesh = ctx->has_mesh;
     out->kernel = ctx->kernel;
+    out->d_state = ctx->d_state;
+    out->nnz_mag = ctx->nnzm_true;
+    out->nnz_phi = ctx->nnzp_true;
     return MM_OK;
 }
 
 int ctx_fail(mm_ctx* ctx, int code, const char* msg) { return fail(ctx, code, "%s", msg); }
+
+int ctx_refresh_state(mm_ctx* ctx) {
+    if (!ctx || !ctx->has_mesh) return MM_ERR_STATE;
+    CK_CUDA(cudaSetDevice(ctx->device));
+    CK_CUDA(cudaMemcpy(ctx->h_state, ctx->d_state, sizeof(mm::DevState), cudaMemcpyDeviceToHost));
+    ctx->has_eval = true;
+    return MM_OK;
+}
 
 }  // namespace mm
 
@@ -412,13 +441,14 @@ int mm_create(mm_ctx** out, const mm_options* opt) {
     if (!coop) return bail(MM_ERR_CUDA);
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     // blocks_per_sm selects the kernel instantiation (register budget) and
-    // the grid: 2, 3, 4 or 6 use the kernels bounded for that occupancy
-    // (0 = 3, the fastest measured on GB300), others the unbounded one.
-    ctx->kernel = mm::solver_kernel(ctx->blocks_per_sm_req > 0 ? ctx->blocks_per_sm_req : 3);
+    // the grid: 2, 3 or 4 blocks per SM (0 or anything else = 3, the fastest
+    // measured on GB300).
+    const int variant = (ctx->blocks_per_sm_req >= 2 && ctx->blocks_per_sm_req <= 4) ? ctx->blocks_per_sm_req : 3;
+    ctx->kernel = mm::solver_kernel(variant);
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ctx->kernel, MM_BLOCK, 0) != cudaSuccess || bps < 1)
         return bail(MM_ERR_CUDA);
-    if (ctx->blocks_per_sm_req > 0) bps = std::min(bps, ctx->blocks_per_sm_req);
+    bps = std::min(bps, variant);
     ctx->blocks = bps * ctx->nsm;
     if (opt && opt->stream) {
         ctx->stream = (cudaStream_t)opt->stream;

@@ -141,6 +141,8 @@ struct CtxView {
     const unsigned char* ident;  // device
     bool has_mesh;
     const void* kernel;          // the solver kernel the context launches
+    DevState* d_state;           // device
+    long long nnz_mag, nnz_phi;  // true nonzeros of the two graphs
 };
 
 }  // namespace mm
@@ -148,8 +150,14 @@ struct CtxView {
 struct mm_ctx;
 namespace mm {
 // Device function pointer of the solver kernel built for at least
-// min_blocks resident blocks per SM (1, 2, 3, 4 or 6; others -> 1).
+// min_blocks resident blocks per SM (2, 3 or 4; others -> 3).
 const void* solver_kernel(int min_blocks);
+// The batched solver kernel (teams of blocks, one problem per team);
+// min_blocks 3 or 4 (others -> 3).
+const void* solver_batch_kernel(int min_blocks);
 __attribute__((visibility("hidden"))) int ctx_view(mm_ctx* ctx, CtxView* out);
 __attribute__((visibility("hidden"))) int ctx_fail(mm_ctx* ctx, int code, const char* msg);
+// Copy the context's device state to its host mirror after work launched
+// elsewhere (a batch) and mark the current state as evaluated.
+__attribute__((visibility("hidden"))) int ctx_refresh_state(mm_ctx* ctx);
 }  // namespace mm

@@ -1,0 +1,6 @@
+// Single-problem solver kernel for at least 3 resident blocks per SM.
+#include "mm_solver_body.cuh"
+
+namespace mm {
+const void* solver_kernel_3() { return (const void*)k_solver<3>; }
+}  // namespace mm

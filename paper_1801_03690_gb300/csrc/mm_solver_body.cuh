@@ -11,6 +11,7 @@
 // li1-li3, line-search branches, beta*ZA, t1-t3) without host round trips or
 // atomics on floating-point data.  Barrier waits are bounded: a wait that
 // runs out sets the device error flag and every block leaves the kernel.
+#pragma once
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -936,11 +937,12 @@ __device__ int minimize(Ctx& C, int& cur) {
 
 }  // namespace
 
-__device__ __forceinline__ void solver_body(const Problem& P) {
+// The solver on one team of nb blocks (this block is number rank).
+__device__ __forceinline__ void solver_body(const Problem& P, int nb, int rank) {
     Ctx C;
     C.P = &P;
-    C.t.nb = gridDim.x;
-    C.t.rank = blockIdx.x;
+    C.t.nb = nb;
+    C.t.rank = rank;
     C.t.count = P.bar;
     C.t.gen = P.bar + 32;
     C.t.err = P.err;
@@ -979,7 +981,7 @@ __device__ __forceinline__ void solver_body(const Problem& P) {
             status = ST_TIMEOUT;
     }
     if (C.t.dead) status = ST_TIMEOUT;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
         DevState* st = P.state;
         st->cur = cur;
         st->status = status;
@@ -1000,21 +1002,29 @@ __device__ __forceinline__ void solver_body(const Problem& P) {
     }
 }
 
-// One instantiation per occupancy target (minimum resident blocks per SM);
-// the host picks one (mm_options.blocks_per_sm, default 0 = no bound).
+// One instantiation per occupancy target (minimum resident blocks per SM),
+// each compiled in its own translation unit (mm_kern_*.cu); the host picks
+// one through solver_kernel() / solver_batch_kernel().
 template <int MINB>
 __global__ void __launch_bounds__(MM_BLOCK, MINB) k_solver(const __grid_constant__ Problem P) {
-    solver_body(P);
+    solver_body(P, (int)gridDim.x, (int)blockIdx.x);
 }
 
-const void* solver_kernel(int min_blocks) {
-    switch (min_blocks) {
-        case 2: return (const void*)k_solver<2>;
-        case 3: return (const void*)k_solver<3>;
-        case 4: return (const void*)k_solver<4>;
-        case 6: return (const void*)k_solver<6>;
-        default: return (const void*)k_solver<1>;
+// Batched form: the grid is split into teams, team j = blocks
+// [team_first[j], team_first[j+1]) runs the solver on problem j.  Teams only
+// synchronise internally, so problems of different sizes and iteration
+// counts proceed independently inside one launch.
+template <int MINB>
+__global__ void __launch_bounds__(MM_BLOCK, MINB) k_solver_batch(const Problem* __restrict__ probs,
+                                                                  const int* __restrict__ team_first, int nteams) {
+    int lo = 0, hi = nteams;                 // team_first[lo] <= blockIdx.x < team_first[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (team_first[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
     }
+    const int first = team_first[lo];
+    solver_body(probs[lo], team_first[lo + 1] - first, (int)blockIdx.x - first);
 }
 
 }  // namespace mm

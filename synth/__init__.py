@@ -8,9 +8,10 @@ method's code.
 """
 from .mesh import Mesh, kuhn_lattice, cube_in_box, jitter_nodes, voronoi_regions
 from .workloads import (Workload, soft_cube, hard_cube, polycrystal_cube,
-                        small_cube, random_unit_vectors, cone_axes)
+                        small_cube, random_unit_vectors, cone_axes, platelet,
+                        platelet_batch)
 
 __all__ = ["Mesh", "kuhn_lattice", "cube_in_box", "jitter_nodes",
            "voronoi_regions", "Workload", "soft_cube", "hard_cube",
            "polycrystal_cube", "small_cube", "random_unit_vectors",
-           "cone_axes"]
+           "cone_axes", "platelet", "platelet_batch"]

@@ -133,3 +133,70 @@ def polycrystal_cube(n_mag=114, edge=200e-9, box_factor=2.0, n_grains=27, seed=3
     return Workload(name=f"polycrystal_{n_grains}g_{n_mag}", mesh=mesh, materials=mats,
                     fields=fields, m0=m0,
                     meta={"edge": edge, "h": h, "seed": seed, "grain_seeds": seeds})
+
+
+def _graded_axis(half_mag, h, half_box, ratio):
+    """Coordinates covering [-half_box, half_box]: uniform spacing h over
+    [-half_mag, half_mag], then spacing growing by `ratio` per cell outward."""
+    n = max(1, int(np.ceil(2 * half_mag / h - 1e-9)))
+    inner = np.linspace(-half_mag, half_mag, n + 1)
+    out = []
+    x, step = half_mag, h
+    while x < half_box - 1e-15:
+        step *= ratio
+        x = min(x + step, half_box)
+        out.append(x)
+    out = np.array(out)
+    return np.concatenate([-out[::-1], inner, out])
+
+
+def platelet(shape, a, b, thickness=5e-9, h=2.5e-9, hz=2.5e-9, air=1.3, ratio=2.0,
+             seed=0, n_fields=51, b_max=0.05):
+    """A permalloy platelet (Sec. 3.2 material class) of the given in-plane
+    shape ('ellipse', 'rectangle' or 'disc'; semi-axes a >= b in x and y)
+    and thickness, on a lattice that is uniform (h in-plane, hz across)
+    over the platelet and graded (growth `ratio`) out to an air box of
+    `air` times the platelet's extent in every direction.  Field along the
+    long axis (x) from +b_max to -b_max tesla in n_fields values."""
+    if shape == "disc":
+        b = a
+    xs = _graded_axis(a, h, air * a, ratio)
+    ys = _graded_axis(b, h, air * a, ratio)
+    zs = _graded_axis(thickness / 2, hz, max(air * a * 0.5, 3 * thickness), ratio)
+    from .mesh import kuhn_lattice
+    xyz, tets, _ = kuhn_lattice(xs, ys, zs)
+    c = xyz[tets].mean(axis=1)
+    inz = np.abs(c[:, 2]) < thickness / 2
+    if shape == "rectangle":
+        inxy = (np.abs(c[:, 0]) < a) & (np.abs(c[:, 1]) < b)
+    else:
+        inxy = (c[:, 0] / a) ** 2 + (c[:, 1] / b) ** 2 < 1.0
+    region = (inz & inxy).astype(np.int32)
+    mesh = Mesh(xyz=xyz, tets=tets, region=region, shape=(len(xs), len(ys), len(zs)),
+                spacing=h, meta={"shape": shape, "a": a, "b": b})
+    mats = _material_table([(0, 0, 0, 0, 0, 1),
+                            (PERMALLOY["Ms"], PERMALLOY["A"], PERMALLOY["K1"], 1, 0, 0)])
+    bx = np.linspace(b_max, -b_max, n_fields)
+    fields = np.stack([bx, np.zeros_like(bx), np.zeros_like(bx)], axis=1)
+    m0 = np.tile([1.0, 0.0, 0.0], (mesh.n_nodes, 1))
+    return Workload(name=f"platelet_{shape}_{2 * a * 1e9:.0f}x{2 * b * 1e9:.0f}", mesh=mesh,
+                    materials=mats, fields=fields, m0=m0, meta={"seed": seed})
+
+
+def platelet_batch(n=64, seed=4, lateral=(100e-9, 500e-9), thickness=5e-9, n_fields=51,
+                   max_cells=160):
+    """n seeded platelets: shape uniform over ellipse/rectangle/disc, long
+    side uniform in `lateral`, aspect ratio U[1, 3] (discs round), in-plane
+    spacing max(2.5 nm, long side / max_cells), 5 nm thick (3 node layers)."""
+    rng = np.random.default_rng(seed)
+    shapes = ["ellipse", "rectangle", "disc"]
+    out = []
+    for k in range(n):
+        shape = shapes[int(rng.integers(0, 3))]
+        L = rng.uniform(*lateral)
+        asp = 1.0 if shape == "disc" else rng.uniform(1.0, 3.0)
+        a, b = L / 2, L / 2 / asp
+        h = max(2.5e-9, L / max_cells)
+        out.append(platelet(shape, a, b, thickness=thickness, h=h, seed=seed * 1000 + k,
+                            n_fields=n_fields))
+    return out
