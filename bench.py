@@ -136,6 +136,68 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ traffic
+KERNEL_SOURCES = ["paper_1801_03690_gb300/csrc/mm_solver_body.cuh",
+                  "paper_1801_03690_gb300/csrc/mm_internal.cuh"]
+PROFILE = "profiles/k_solver_hard_cube.md"
+
+
+def kernel_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_ratio():
+    """DRAM bytes / algorithmic bytes of the solver kernel from the last ncu
+    capture summarised in profiles/ (a line 'traffic_ratio: R sources: D'),
+    or None when the kernel sources changed since that capture."""
+    try:
+        for line in open(os.path.join(ROOT, PROFILE)):
+            if line.startswith("traffic_ratio:"):
+                f = line.split()
+                if f[3] == kernel_source_digest():
+                    return float(f[1])
+    except (OSError, IndexError, ValueError):
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ ranks
+class Ranks:
+    """Replicas only: every rank solves its own copy of the workload; the
+    only collectives are the timing barrier and the max/sum of the scalar
+    results over ranks."""
+
+    def __init__(self, world, device):
+        self.world = world
+        self.device = device
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(x)], device=self.device, dtype=torch.float64)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.MAX if self.world > 1 else None)
+
+    def sum(self, x):
+        import torch.distributed as dist
+        return self._reduce(x, dist.ReduceOp.SUM if self.world > 1 else None)
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_sample(wl, max_iter, warm_iter=0):
     """The CPU oracle as it stands: assemble, then Algorithm 4 at the first
@@ -208,25 +270,8 @@ def main():
     sz = mag.sizes()
     stream = torch.cuda.ExternalStream(mag.stream, device=torch.device("cuda", local_rank))
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        return float(t.item())
+    ranks = Ranks(world, torch.device("cuda", local_rank))
+    barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
     def run_form(precision):
         """W untimed field steps from m0, then K timed field steps."""
@@ -306,6 +351,7 @@ def main():
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     achieved = x1["bytes"] / (x1["kern_ms"] / 1000.0) / 1e9
+    ratio = traffic_ratio()
     ach64 = fp64["bytes"] / (fp64["kern_ms"] / 1000.0) / 1e9
     dm = float(np.abs(x1["m"] - fp64["m"]).max())
     line = {
@@ -314,7 +360,8 @@ def main():
         "dtype": "fp32+fp64", "data": "synthetic",
         "config": workload_desc(args.workload, wl, sz),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "k_solver",
+                     "frac": achieved / hbm,
+                     "traffic": (ratio * x1["bytes"] / K) if ratio else None, "kernel": "k_solver",
                      "peak_source": peak_src, "alg_bytes_per_launch": x1["bytes"] / K,
                      "kernel_ms_per_launch": x1["kern_ms"] / K},
         "plain_fp64": {"value": fp64["value"], "unit": UNIT, "ms_per_step": fp64["t_ms"] / K,

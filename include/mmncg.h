@@ -258,6 +258,48 @@ int mm_batch_autotune(mm_batch* b, const mm_params* p, int* chosen_blocks_per_sm
 /* Device time (ms) of the last batch launch or curve. */
 int mm_batch_last_ms(mm_batch* b, double* ms);
 
+/* ---- Learned warm start (no counterpart in the paper).  A per-node
+ * multilayer perceptron 16 -> 128 -> 128 -> 128 -> 4 (ReLU) maps local
+ * features of a converged state and the next field increment to a
+ * correction of m and of the scalar potential; Algorithm 4 then runs to
+ * t1-t3 from the corrected state as usual, so the network only moves the
+ * starting point.  Forward and backward passes run on the tensor cores
+ * (BF16 operands, FP32 accumulation); FP32 master weights and Adam.
+ * Parameters (floats): W1 [128][16], b1, W2 [128][128], b2, W3, b3,
+ * W4 [4][128], b4, weights row-major [out][in]. */
+typedef struct mm_mlp mm_mlp;
+int64_t mm_mlp_param_count(void);
+/* He-uniform initial weights from a seeded generator, zero biases. */
+int mm_mlp_create(mm_mlp** mlp, int device, uint64_t seed);
+void mm_mlp_destroy(mm_mlp* mlp);
+int mm_mlp_set_params(mm_mlp* mlp, const float* params, int64_t count);
+int mm_mlp_get_params(mm_mlp* mlp, float* params, int64_t count);
+/* Input standardisation applied in FP32 before the BF16 first layer:
+ * x_c <- (x_c - mean[c]) / std[c] (default mean 0, std 1). */
+int mm_mlp_set_input_norm(mm_mlp* mlp, const float mean[16], const float stdev[16]);
+/* Y_dev [n][4] = network(X_dev [n][16]) (device arrays); synchronises. */
+int mm_mlp_forward(mm_mlp* mlp, const float* X_dev, int64_t n, float* Y_dev);
+/* Mean squared error over all outputs against T_dev [n][4] and its gradient
+ * (host array in the parameter layout, may be NULL); no update. */
+int mm_mlp_gradient(mm_mlp* mlp, const float* X_dev, const float* T_dev, int64_t n,
+                    float* grad_host, float* loss_out);
+/* One Adam step (beta 0.9 / 0.999) on the mean squared error; loss_out may
+ * be NULL (then no synchronisation). */
+int mm_mlp_train_step(mm_mlp* mlp, const float* X_dev, const float* T_dev, int64_t n,
+                      float lr, float* loss_out);
+/* Features of every magnetic node of the context's current state for the
+ * step to the applied field mu0h_next (tesla): m, effective field, exchange
+ * field, anisotropy field (fields per unit Ms weight, internal units), the
+ * field increment (internal units) and the scalar potential at the node.
+ * X_dev [n_mag][16] floats, magnetic nodes in ascending node id. */
+int mm_warmstart_features(mm_ctx* ctx, const double mu0h_next[3], float* X_dev);
+/* Predict and apply the warm start for the step to mu0h_next:
+ * m_i <- N(m_i + scale_m |dh| y_i[0:3]), phi_i += scale_phi |dh| y_i[3] on the
+ * magnetic nodes (|dh| = norm of the field increment in internal units).
+ * Then set the field and call mm_minimize as usual. */
+int mm_warmstart_apply(mm_ctx* ctx, mm_mlp* mlp, const double mu0h_next[3],
+                       double scale_m, double scale_phi);
+
 /* Device time (ms) of the last persistent-kernel launch, from CUDA events
  * on the context's stream; synchronises. */
 int mm_last_kernel_ms(mm_ctx* ctx, double* ms);

@@ -85,6 +85,20 @@ EXPORTS = {
     "mm_batch_autotune": (C.c_int, [C.c_void_p, C.POINTER(mm_params), C.POINTER(C.c_int),
                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mm_batch_last_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mm_mlp_param_count": (C.c_int64, []),
+    "mm_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_uint64]),
+    "mm_mlp_destroy": (None, [C.c_void_p]),
+    "mm_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "mm_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "mm_mlp_set_input_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mm_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mm_mlp_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                  C.POINTER(C.c_float)]),
+    "mm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                    C.POINTER(C.c_float)]),
+    "mm_warmstart_features": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "mm_warmstart_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_double,
+                                     C.c_double]),
     "mm_energy_gradient_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mm_params),
                                              C.c_void_p, C.c_int, C.c_void_p]),
     "mm_stream": (C.c_void_p, [C.c_void_p]),

@@ -289,3 +289,94 @@ class Batch:
         ms = C.c_double()
         self._check(self._lib.mm_batch_last_ms(self._h, C.byref(ms)))
         return ms.value
+
+
+class MLP:
+    """The warm-start network (16 -> 128 -> 128 -> 128 -> 4), trained and
+    evaluated by the library's tensor-core kernels."""
+
+    def __init__(self, device=0, seed=0):
+        self._lib = L.load()
+        h = C.c_void_p()
+        rc = self._lib.mm_mlp_create(C.byref(h), int(device), C.c_uint64(seed))
+        if rc != 0:
+            raise MMError(rc, "mm_mlp_create failed")
+        self._h = h
+        self.device = device
+        self.n_params = int(self._lib.mm_mlp_param_count())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        f = np.ascontiguousarray(flat, dtype=np.float32)
+        rc = self._lib.mm_mlp_set_params(self._h, f.ctypes.data_as(C.c_void_p), f.size)
+        if rc:
+            raise MMError(rc, "mm_mlp_set_params")
+
+    def set_input_norm(self, mean, stdev):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        s = np.ascontiguousarray(stdev, dtype=np.float32)
+        rc = self._lib.mm_mlp_set_input_norm(self._h, m.ctypes.data_as(C.c_void_p), s.ctypes.data_as(C.c_void_p))
+        if rc:
+            raise MMError(rc, "mm_mlp_set_input_norm")
+
+    def get_params(self):
+        f = np.zeros(self.n_params, dtype=np.float32)
+        rc = self._lib.mm_mlp_get_params(self._h, f.ctypes.data_as(C.c_void_p), f.size)
+        if rc:
+            raise MMError(rc, "mm_mlp_get_params")
+        return f
+
+    def forward(self, X):
+        import torch
+        assert X.is_cuda and X.dtype == torch.float32 and X.shape[1] == 16 and X.is_contiguous()
+        Y = torch.empty((X.shape[0], 4), dtype=torch.float32, device=X.device)
+        torch.cuda.synchronize()
+        rc = self._lib.mm_mlp_forward(self._h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr()))
+        if rc:
+            raise MMError(rc, "mm_mlp_forward")
+        return Y
+
+    def gradient(self, X, T):
+        import torch
+        torch.cuda.synchronize()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_float()
+        rc = self._lib.mm_mlp_gradient(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                       X.shape[0], g.ctypes.data_as(C.c_void_p), C.byref(loss))
+        if rc:
+            raise MMError(rc, "mm_mlp_gradient")
+        return g, loss.value
+
+    def train_step(self, X, T, lr, want_loss=False):
+        loss = C.c_float()
+        rc = self._lib.mm_mlp_train_step(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                         X.shape[0], C.c_float(lr), C.byref(loss) if want_loss else None)
+        if rc:
+            raise MMError(rc, "mm_mlp_train_step")
+        return loss.value if want_loss else None
+
+
+def warmstart_features(mag, mu0h_next, n_mag):
+    """Features [n_mag, 16] (float32, device) of the current state of `mag`
+    for the step to mu0h_next."""
+    import torch
+    X = torch.empty((n_mag, 16), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    b = (C.c_double * 3)(*[float(v) for v in mu0h_next])
+    mag._check(mag._lib.mm_warmstart_features(mag._h, b, C.c_void_p(X.data_ptr())))
+    return X
+
+
+def warmstart_apply(mag, mlp, mu0h_next, scale_m, scale_phi):
+    b = (C.c_double * 3)(*[float(v) for v in mu0h_next])
+    mag._check(mag._lib.mm_warmstart_apply(mag._h, mlp._h, b, float(scale_m), float(scale_phi)))

@@ -93,21 +93,38 @@ __device__ __forceinline__ double warp_max(double v) {
 // Reduce NS sums and NX maxima over the team.  Deterministic: fixed order
 // within warps (shfl_down tree, lane 0), across warps (ascending) and across
 // blocks (ascending strided accumulation, then the same block tree).
-template <int NS, int NX>
-__device__ bool team_reduce(Team& t, double (&s)[NS > 0 ? NS : 1], double (&x)[NX > 0 ? NX : 1]) {
+template <typename AT>
+__device__ __forceinline__ AT warp_sum_t(AT v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename AT>
+__device__ __forceinline__ AT warp_max_t(AT v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// AT is the type of the per-thread and per-warp accumulation (float for the
+// FP32 phases, whose sums are all of positive terms); the combination across
+// warps and blocks is always FP64.
+template <int NS, int NX, typename AT = double>
+__device__ bool team_reduce(Team& t, AT (&s)[NS > 0 ? NS : 1], AT (&x)[NX > 0 ? NX : 1]) {
     static_assert(NS + NX <= MM_MAXRED, "too many reduction values");
     __shared__ double sh[MM_MAXRED][kWarps];
     __shared__ double res[MM_MAXRED];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        double v = warp_sum(s[k]);
-        if (lane == 0) sh[k][warp] = v;
+        AT v = warp_sum_t<AT>(s[k]);
+        if (lane == 0) sh[k][warp] = (double)v;
     }
 #pragma unroll
     for (int k = 0; k < NX; ++k) {
-        double v = warp_max(x[k]);
-        if (lane == 0) sh[NS + k][warp] = v;
+        AT v = warp_max_t<AT>(x[k]);
+        if (lane == 0) sh[NS + k][warp] = (double)v;
     }
     __syncthreads();
     double* part = t.part + (size_t)(t.epoch & 1) * MM_MAXRED * t.nb;
@@ -137,9 +154,52 @@ __device__ bool team_reduce(Team& t, double (&s)[NS > 0 ? NS : 1], double (&x)[N
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NS; ++k) s[k] = res[k];
+    for (int k = 0; k < NS; ++k) s[k] = (AT)res[k];
 #pragma unroll
-    for (int k = 0; k < NX; ++k) x[k] = res[NS + k];
+    for (int k = 0; k < NX; ++k) x[k] = (AT)res[NS + k];
+    __syncthreads();
+    return true;
+}
+
+// Team sums accumulated in FP32 per thread and warp, returned in FP64.
+template <int NS>
+__device__ bool team_sum_f32(Team& t, float (&s)[NS], double (&out)[NS]) {
+    __shared__ double sh[MM_MAXRED][kWarps];
+    __shared__ double res[MM_MAXRED];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const float v = warp_sum_t<float>(s[k]);
+        if (lane == 0) sh[k][warp] = (double)v;
+    }
+    __syncthreads();
+    double* part = t.part + (size_t)(t.epoch & 1) * MM_MAXRED * t.nb;
+    if (threadIdx.x < NS) {
+        const int k = threadIdx.x;
+        double a = sh[k][0];
+        for (int w = 1; w < kWarps; ++w) a += sh[k][w];
+        part[(size_t)k * t.nb + t.rank] = a;
+    }
+    t.epoch++;
+    if (!team_sync(t)) return false;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const double* pk = part + (size_t)k * t.nb;
+        double a = 0.0;
+        for (int j = threadIdx.x; j < t.nb; j += MM_BLOCK) a += pk[j];
+        a = warp_sum(a);
+        if (lane == 0) sh[k][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+        const int k = threadIdx.x;
+        double a = sh[k][0];
+        for (int w = 1; w < kWarps; ++w) a += sh[k][w];
+        res[k] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NS; ++k) out[k] = res[k];
     __syncthreads();
     return true;
 }
@@ -367,20 +427,20 @@ __device__ bool ph_pzero(Ctx& C) {
 __device__ bool ph_p32_init(Ctx& C, double& rz, double& rr) {
     const Problem& P = *C.P;
     Team& t = C.t;
-    double acc[2] = {0.0, 0.0};
-    double dummy[1] = {0.0};
+    float acc[2] = {0.0f, 0.0f};
+    double out[2];
     ROWS(p, P.nphi) {
         const float r = (float)P.pres[p];
         const float z = r * P.dinvP32[p];
         P.pres32[p] = r;
         P.pprec32[p] = z;
         P.pdelta32[p] = 0.0f;
-        acc[0] += (double)r * (double)z;
-        acc[1] += (double)r * (double)r;
+        acc[0] += r * z;
+        acc[1] += r * r;
     }
-    if (!team_reduce<2, 0>(t, acc, dummy)) return false;
-    rz = acc[0];
-    rr = acc[1];
+    if (!team_sum_f32<2>(t, acc, out)) return false;
+    rz = out[0];
+    rr = out[1];
     return true;
 }
 
@@ -388,8 +448,8 @@ __device__ bool ph_p32_init(Ctx& C, double& rz, double& rr) {
 __device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
     const Problem& P = *C.P;
     Team& t = C.t;
-    double acc[1] = {0.0};
-    double dummy[1] = {0.0};
+    float acc[1] = {0.0f};
+    double out[1];
     const bool first = (beta == 0.0f);
     const float* z = P.pprec32;
     ROWS(p, P.nphi) {
@@ -398,10 +458,10 @@ __device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
         const float qn = first ? s : s + beta * P.pq32[p];
         P.pdir32[p] = dn;
         P.pq32[p] = qn;
-        acc[0] += (double)dn * (double)qn;
+        acc[0] += dn * qn;
     }
-    if (!team_reduce<1, 0>(t, acc, dummy)) return false;
-    dq = acc[0];
+    if (!team_sum_f32<1>(t, acc, out)) return false;
+    dq = out[0];
     return true;
 }
 
@@ -409,20 +469,20 @@ __device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
 __device__ bool ph_p32_update(Ctx& C, float a, double& rz, double& rr) {
     const Problem& P = *C.P;
     Team& t = C.t;
-    double acc[2] = {0.0, 0.0};
-    double dummy[1] = {0.0};
+    float acc[2] = {0.0f, 0.0f};
+    double out[2];
     ROWS(p, P.nphi) {
         P.pdelta32[p] += a * P.pdir32[p];
         const float r = P.pres32[p] - a * P.pq32[p];
         const float z = r * P.dinvP32[p];
         P.pres32[p] = r;
         P.pprec32[p] = z;
-        acc[0] += (double)r * (double)z;
-        acc[1] += (double)r * (double)r;
+        acc[0] += r * z;
+        acc[1] += r * r;
     }
-    if (!team_reduce<2, 0>(t, acc, dummy)) return false;
-    rz = acc[0];
-    rr = acc[1];
+    if (!team_sum_f32<2>(t, acc, out)) return false;
+    rz = out[0];
+    rr = out[1];
     return true;
 }
 

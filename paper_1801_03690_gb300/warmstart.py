@@ -1,0 +1,80 @@
+"""Learned warm start: collect training pairs from the method's own
+demagnetisation-curve trajectories, train the network with the library's
+tensor-core kernels, and run a curve with the warm start applied before
+every minimisation (Algorithm 4 still runs to t1-t3 from the corrected
+state).
+
+Training pairs: at the converged state of field step k, the features for the
+step to field k+1 (mm_warmstart_features) and the targets
+((m_{k+1} - m_k), (phi_{k+1} - phi_k)) / |dh| on the magnetic nodes, where
+|dh| is the norm of the field increment in internal units.  The network
+standardises its inputs itself (FP32, before the BF16 first layer;
+features such as m_z = 0.999 +- 0.001 would lose their signal if the
+standardisation were folded into BF16 weights); targets are standardised
+for training and their scales become the scale_m / scale_phi arguments of
+mm_warmstart_apply.
+"""
+from .api import Params, warmstart_features, warmstart_apply
+
+
+def collect(mag, m0, fields, n_mag, params=None):
+    """Run the curve on `mag` from m0 and return device tensors (X, T, nli)."""
+    import torch
+    prm = params or Params()
+    mag.set_magnetization(m0)
+    mag.set_field(fields[0])
+    nli = mag.minimize(prm)["nli"]
+    Xs, Ts = [], []
+    for k in range(len(fields) - 1):
+        X = warmstart_features(mag, fields[k + 1], n_mag)
+        mag.set_field(fields[k + 1])
+        nli += mag.minimize(prm)["nli"]
+        X1 = warmstart_features(mag, fields[k + 1], n_mag)
+        dh = float(torch.linalg.vector_norm(X[0, 12:15]).item())
+        if dh == 0.0:
+            continue
+        T = torch.cat([X1[:, 0:3] - X[:, 0:3], X1[:, 15:16] - X[:, 15:16]], dim=1) / dh
+        Xs.append(X)
+        Ts.append(T)
+    return torch.cat(Xs), torch.cat(Ts), nli
+
+
+def train(mlp, X, T, steps=2000, batch=16384, lr=2e-3, seed=0, log_every=0):
+    """Set the network's input standardisation from X, train with Adam on
+    random mini-batches of standardised targets.  Returns
+    (scale_m, scale_phi, losses)."""
+    import torch
+    mu = X.mean(0)
+    sd = X.std(0)
+    sd = torch.where(sd > 1e-6 * (mu.abs() + 1.0), sd, torch.ones_like(sd))   # constant features: centre only
+    mlp.set_input_norm(mu.cpu().numpy(), sd.cpu().numpy())
+    s_m = float(T[:, 0:3].std().clamp_min(1e-12).item())
+    s_p = float(T[:, 3].std().clamp_min(1e-12).item())
+    Tn = torch.cat([T[:, 0:3] / s_m, T[:, 3:4] / s_p], dim=1).contiguous()
+    g = torch.Generator(device=X.device)
+    g.manual_seed(seed)
+    n = X.shape[0]
+    losses = []
+    for it in range(steps):
+        idx = torch.randint(0, n, (min(batch, n),), device=X.device, generator=g)
+        xb = X[idx].contiguous()
+        tb = Tn[idx].contiguous()
+        want = bool(log_every) and (it % log_every == 0 or it == steps - 1)
+        loss = mlp.train_step(xb, tb, lr, want_loss=want)
+        if want:
+            losses.append((it, loss))
+    return s_m, s_p, losses
+
+
+def curve(mag, m0, fields, params=None, mlp=None, scales=None):
+    """Demagnetisation curve; with `mlp`, the warm start is applied before
+    every field step after the first.  Returns (stats per step, total nli)."""
+    prm = params or Params()
+    mag.set_magnetization(m0)
+    out = []
+    for k, b in enumerate(fields):
+        if mlp is not None and k > 0:
+            warmstart_apply(mag, mlp, b, scales[0], scales[1])
+        mag.set_field(b)
+        out.append(mag.minimize(prm))
+    return out, sum(s["nli"] for s in out)

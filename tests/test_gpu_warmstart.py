@@ -1,0 +1,102 @@
+"""The learned warm start: the tensor-core network against the CPU
+reference network, training, and what the trained network gains over the
+method without it on a demagnetisation curve."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+def _params_list(flat):
+    sizes = omlp.SIZES
+    out, o = [], 0
+    for n_in, n_out in zip(sizes[:-1], sizes[1:]):
+        W = flat[o:o + n_in * n_out].reshape(n_out, n_in).astype(np.float64)
+        o += n_in * n_out
+        b = flat[o:o + n_out].astype(np.float64)
+        o += n_out
+        out.append((W, b))
+    return out
+
+
+def test_forward_matches_reference():
+    import torch
+    from paper_1801_03690_gb300 import MLP
+    net = MLP(seed=3)
+    p = net.get_params()
+    p[16 * 128:16 * 128 + 128] = np.random.default_rng(0).normal(size=128) * 0.1   # nonzero b1
+    net.set_params(p)
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(301, 16)).astype(np.float32)          # ragged tail
+    Y = net.forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    Yr, _ = omlp.forward(_params_list(p), X.astype(np.float64), round_bf16=True)
+    scale = np.abs(Yr).max()
+    np.testing.assert_allclose(Y, Yr, rtol=0, atol=1e-2 * scale)
+
+
+def test_gradient_matches_reference():
+    import torch
+    from paper_1801_03690_gb300 import MLP
+    net = MLP(seed=5)
+    p = net.get_params()
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(517, 16)).astype(np.float32)
+    T = rng.normal(size=(517, 4)).astype(np.float32)
+    g, loss = net.gradient(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"))
+    lr, gr = omlp.loss_and_grads(_params_list(p), X.astype(np.float64), T.astype(np.float64),
+                                 round_bf16=True)
+    assert loss == pytest.approx(lr, rel=1e-2)
+    gflat = _params_list(g)
+    for l, ((gw, gb), (rw, rb)) in enumerate(zip(gflat, gr)):
+        sw, sb = np.abs(rw).max(), np.abs(rb).max()
+        np.testing.assert_allclose(gw, rw, rtol=0, atol=3e-2 * sw, err_msg=f"W{l + 1}")
+        np.testing.assert_allclose(gb, rb, rtol=0, atol=3e-2 * sb, err_msg=f"b{l + 1}")
+
+
+def test_training_fits_a_smooth_map():
+    import torch
+    from paper_1801_03690_gb300 import MLP
+    net = MLP(seed=7)
+    rng = np.random.default_rng(3)
+    X = torch.tensor(rng.normal(size=(20000, 16)), dtype=torch.float32, device="cuda")
+    R = torch.tensor(rng.normal(size=(16, 4)) / 4, dtype=torch.float32, device="cuda")
+    T = torch.tanh(X @ R).contiguous()
+    first = net.train_step(X[:4096].contiguous(), T[:4096].contiguous(), 1e-3, want_loss=True)
+    for i in range(400):
+        j = (i * 4096) % (20000 - 4096)
+        net.train_step(X[j:j + 4096].contiguous(), T[j:j + 4096].contiguous(), 1e-3)
+    _, last = net.gradient(X, T)
+    assert last < 0.2 * first
+
+
+def test_warm_start_gain_on_a_demag_curve():
+    """Train on the method's own trajectory of one jittered hard-magnetic
+    cube, then run the curve of another jitter of it with and without the
+    warm start: the corrected starts must not change the curve (NCG runs to
+    t1-t3 either way) and must save NCG iterations."""
+    import torch
+    from paper_1801_03690_gb300 import MLP, Magnet, Params, warmstart
+    prm = Params(jmax=4, precision=1)
+    train_wl = synth.hard_cube(n_mag=10, seed=2, n_fields=40)
+    test_wl = synth.hard_cube(n_mag=10, seed=9, n_fields=40)
+    fields = train_wl.fields[:16]                 # 0 .. -3.1 T: reversible part of the curve
+    mag = Magnet()
+    mag.upload_workload(train_wl)
+    n_mag = mag.sizes()["n_mag"]
+    X, T, _ = warmstart.collect(mag, train_wl.m0, fields, n_mag, prm)
+    net = MLP(seed=11)
+    s_m, s_p, _ = warmstart.train(net, X, T, steps=600, batch=8192, lr=2e-3)
+    mag.close()
+    mag = Magnet()
+    mag.upload_workload(test_wl)
+    base, nli_base = warmstart.curve(mag, test_wl.m0, fields, prm)
+    warm, nli_warm = warmstart.curve(mag, test_wl.m0, fields, prm, mlp=net, scales=(s_m, s_p))
+    assert all(s["status"] == "ok" for s in base + warm)
+    Mb = np.array([s["M"] for s in base])
+    Mw = np.array([s["M"] for s in warm])
+    np.testing.assert_allclose(Mw, Mb, atol=1e-4)
+    print(f"NCG iterations without / with the warm start: {nli_base} / {nli_warm}")
+    assert nli_warm < nli_base
