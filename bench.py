@@ -230,6 +230,14 @@ def main():
     ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "medium", "soft_cube", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch"],
+                    help="steps: the timed field steps (default line); curve: full demagnetisation "
+                         "curves of the plain FP64, precision and precision + learned forms; "
+                         "batch: the batched platelet workload")
+    ap.add_argument("--n-platelets", type=int, default=64)
+    ap.add_argument("--forms", default="plain_fp64,precision,precision_learned")
+    ap.add_argument("--max-change", type=float, default=0.02,
+                    help="warm start: cap on the largest predicted nodal change")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="solver kernel instantiation / grid (0 = default)")
     args = ap.parse_args()
@@ -260,6 +268,11 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local_rank)
     from paper_1801_03690_gb300 import Magnet, Params
+
+    if args.mode == "curve":
+        return curve_mode(args, rank, local_rank)
+    if args.mode == "batch":
+        return batch_mode(args, rank, local_rank)
 
     wl = workload(args.workload)
     fields = wl.fields
@@ -387,6 +400,159 @@ def main():
                                 "sample": desc}
     print(json.dumps(line))
     mag.close()
+    return 0
+
+
+def curve_mode(args, rank, local_rank):
+    """Full demagnetisation curves of one workload in three forms: plain
+    FP64, the precision form, and the precision form with the learned warm
+    start (network trained on the curve of a coarser mesh of the same
+    recipe).  Reports wall time, NCG iterations and coercive field."""
+    import torch
+    from paper_1801_03690_gb300 import Magnet, Params, MLP, warmstart
+    from paper_1801_03690_gb300.curves import coercive_field
+    wl = workload(args.workload)
+    fields = wl.fields
+    mag = Magnet(device=local_rank, blocks_per_sm=args.blocks_per_sm)
+    mag.upload_workload(wl)
+    sz = mag.sizes()
+    out = {}
+
+    forms = args.forms.split(",")
+
+    def run(name, prm, net=None, scales=None):
+        if name not in forms:
+            return
+        mag.set_magnetization(wl.m0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sts = []
+        for k, b in enumerate(fields):
+            if net is not None and k > 0:
+                warmstart.warmstart_apply(mag, net, b, scales[0], scales[1], args.max_change)
+            mag.set_field(b)
+            sts.append(mag.minimize(prm))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        M = np.array([s["M"] for s in sts])
+        out[name] = {"wall_s": wall, "nli": int(sum(s["nli"] for s in sts)),
+                     "evals": int(sum(s["evals"] for s in sts)), "mi": int(sum(s["mi"] for s in sts)),
+                     "Hc_T": coercive_field(fields, M),
+                     "statuses": sorted(set(s["status"] for s in sts)),
+                     "nli_per_step": [int(s["nli"]) for s in sts], "Mz": M[:, 2].tolist()}
+
+    run("plain_fp64", Params(precision=0))
+    run("precision", Params(precision=1))
+    # learned warm start: train on the curve of the same recipe at half the resolution
+    if "precision_learned" not in forms:
+        if rank == 0:
+            print(json.dumps({"mode": "curve", "workload": wl.name, "sizes": sz, "forms": out}))
+        return 0
+    t0 = time.perf_counter()
+    import synth
+    coarse = synth.hard_cube(n_mag=max(8, wl.meta.get("n_mag", 48) // 2), seed=12,
+                             n_fields=len(fields)) if args.workload == "hard_cube" else None
+    if coarse is None:
+        coarse = synth.hard_cube(n_mag=12, seed=12, n_fields=len(fields))
+    tm = Magnet(device=local_rank)
+    tm.upload_workload(coarse)
+    X, T, _ = warmstart.collect(tm, coarse.m0, coarse.fields, tm.sizes()["n_mag"], Params(precision=1))
+    tm.close()
+    net = MLP(device=local_rank, seed=11)
+    s_m, s_p, losses = warmstart.train(net, X, T, steps=1500, batch=16384, lr=2e-3, log_every=500)
+    train_s = time.perf_counter() - t0
+    run("precision_learned", Params(precision=1), net=net, scales=(s_m, s_p))
+    ref = out.get("plain_fp64") or out.get("precision")
+    for k in ("precision", "precision_learned"):
+        if k not in out or out[k] is ref:
+            continue
+        o = out[k]
+        o["speedup_vs_plain_fp64"] = ref["wall_s"] / o["wall_s"]
+        if o["Hc_T"] is not None and ref["Hc_T"] is not None:
+            o["Hc_rel_diff"] = abs(o["Hc_T"] - ref["Hc_T"]) / ref["Hc_T"]
+        o["max_abs_dMz"] = float(np.max(np.abs(np.array(o["Mz"]) - np.array(ref["Mz"]))))
+    out["precision_learned"]["training"] = {"samples": int(X.shape[0]), "steps": 1500, "seconds": train_s,
+                                            "losses": losses, "trained_on": coarse.name,
+                                            "max_change": args.max_change}
+    if rank == 0:
+        print(json.dumps({"mode": "curve", "workload": wl.name, "sizes": sz, "n_fields": len(fields),
+                          "forms": out}))
+    mag.close()
+    return 0
+
+
+def batch_mode(args, rank, local_rank):
+    """The batched sensor workload: n permalloy platelets of 5k-80k magnetic
+    nodes, minimised at one field in one persistent launch (after the
+    autotuner picked the kernel instantiation and team split), against the
+    same problems minimised one after the other."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import synth
+    from paper_1801_03690_gb300 import Magnet, Params, Batch
+    wls = synth.platelet_batch(args.n_platelets)
+    prm = Params(precision=1)
+
+    def make(wl):
+        m = Magnet(device=local_rank)
+        m.upload_workload(wl)
+        return m
+
+    with ThreadPoolExecutor(8) as ex:
+        mags = list(ex.map(make, wls))
+    sizes = [m.sizes() for m in mags]
+
+    def reset(k):
+        for m, wl in zip(mags, wls):
+            m.set_magnetization(wl.m0)
+            m.set_field(wl.fields[k])
+
+    res = {}
+    reset(0)
+    batch = Batch(mags)
+    bps, gamma, ms = batch.autotune(prm)
+    res["autotune"] = {"blocks_per_sm": bps, "gamma": gamma, "trial_ms": ms}
+    for k in (0, 1, 2):                               # warm-up field steps
+        reset(k) if k == 0 else [m.set_field(wl.fields[k]) for m, wl in zip(mags, wls)]
+        batch.minimize(prm)
+    K = 5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nli = 0
+    for k in range(3, 3 + K):
+        for m, wl in zip(mags, wls):
+            m.set_field(wl.fields[k])
+        sts = batch.minimize(prm)
+        nli += sum(s["nli"] for s in sts)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    res["batched"] = {"nli": nli, "seconds": tb, "NCG_it_per_s": nli / tb}
+    # the same field steps one problem after the other
+    reset(0)
+    for k in (0, 1, 2):
+        for m, wl in zip(mags, wls):
+            m.set_field(wl.fields[k])
+            m.minimize(prm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nli_s = 0
+    for k in range(3, 3 + K):
+        for m, wl in zip(mags, wls):
+            m.set_field(wl.fields[k])
+            nli_s += m.minimize(prm)["nli"]
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    res["sequential"] = {"nli": nli_s, "seconds": ts, "NCG_it_per_s": nli_s / ts}
+    res["speedup"] = ts / tb
+    if rank == 0:
+        print(json.dumps({"mode": "batch", "n": len(wls),
+                          "n_mag_total": int(sum(s["n_mag"] for s in sizes)),
+                          "n_phi_total": int(sum(s["n_phi"] for s in sizes)),
+                          "n_mag_range": [int(min(s["n_mag"] for s in sizes)), int(max(s["n_mag"] for s in sizes))],
+                          "field_steps_timed": K, **res}))
+    batch.close()
+    for m in mags:
+        m.close()
     return 0
 
 

@@ -294,11 +294,14 @@ int mm_mlp_train_step(mm_mlp* mlp, const float* X_dev, const float* T_dev, int64
  * X_dev [n_mag][16] floats, magnetic nodes in ascending node id. */
 int mm_warmstart_features(mm_ctx* ctx, const double mu0h_next[3], float* X_dev);
 /* Predict and apply the warm start for the step to mu0h_next:
- * m_i <- N(m_i + scale_m |dh| y_i[0:3]), phi_i += scale_phi |dh| y_i[3] on the
- * magnetic nodes (|dh| = norm of the field increment in internal units).
+ * m_i <- N(m_i + c scale_m |dh| y_i[0:3]), phi_i += c scale_phi |dh| y_i[3] on
+ * the magnetic nodes (|dh| = norm of the field increment in internal
+ * units), c = min(1, max_change / max_i |predicted change of m_i|) when
+ * max_change > 0 (a cap that keeps the prediction from carrying the state
+ * over a small energy barrier; the minimiser must follow the local minimum).
  * Then set the field and call mm_minimize as usual. */
 int mm_warmstart_apply(mm_ctx* ctx, mm_mlp* mlp, const double mu0h_next[3],
-                       double scale_m, double scale_phi);
+                       double scale_m, double scale_phi, double max_change);
 
 /* Device time (ms) of the last persistent-kernel launch, from CUDA events
  * on the context's stream; synchronises. */

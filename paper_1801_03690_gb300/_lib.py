@@ -98,7 +98,7 @@ EXPORTS = {
                                     C.POINTER(C.c_float)]),
     "mm_warmstart_features": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "mm_warmstart_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_double,
-                                     C.c_double]),
+                                     C.c_double, C.c_double]),
     "mm_energy_gradient_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mm_params),
                                              C.c_void_p, C.c_int, C.c_void_p]),
     "mm_stream": (C.c_void_p, [C.c_void_p]),

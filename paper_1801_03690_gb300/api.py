@@ -377,6 +377,7 @@ def warmstart_features(mag, mu0h_next, n_mag):
     return X
 
 
-def warmstart_apply(mag, mlp, mu0h_next, scale_m, scale_phi):
+def warmstart_apply(mag, mlp, mu0h_next, scale_m, scale_phi, max_change=0.02):
     b = (C.c_double * 3)(*[float(v) for v in mu0h_next])
-    mag._check(mag._lib.mm_warmstart_apply(mag._h, mlp._h, b, float(scale_m), float(scale_phi)))
+    mag._check(mag._lib.mm_warmstart_apply(mag._h, mlp._h, b, float(scale_m), float(scale_phi),
+                                           float(max_change)))

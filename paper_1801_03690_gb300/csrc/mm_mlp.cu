@@ -495,24 +495,37 @@ __global__ void k_features(int nm, const mm::Problem* Pp, const mm::DevState* st
     f[15] = (float)P.phi[i];
 }
 
-// m_i <- N(m_i + sm |dh| y_i[0:3]);  phi_i += sphi |dh| y_i[3] (magnetic rows).
+// Largest predicted nodal change max_i |sm |dh| y_i[0:3]| (non-negative
+// floats compare like their bit patterns).
+__global__ void k_apply_max(int nm, const float* Y, double sm, double dhn, unsigned* mx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    const float* y = Y + (size_t)i * NOUT;
+    const float d = (float)(sm * dhn * sqrt((double)y[0] * y[0] + (double)y[1] * y[1] + (double)y[2] * y[2]));
+    if (isfinite(d)) atomicMax(mx, __float_as_uint(d));
+}
+
+// m_i <- N(m_i + c sm |dh| y_i[0:3]);  phi_i += c sphi |dh| y_i[3] (magnetic
+// rows), c = min(1, cap / max_i |predicted change|).
 __global__ void k_apply(int nm, const mm::Problem* Pp, const mm::DevState* st, const float* Y, double sm,
-                        double sphi, double dhn) {
+                        double sphi, double dhn, double cap, const unsigned* mx) {
     const mm::Problem& P = *Pp;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nm) return;
+    const double big = (double)__uint_as_float(*mx);
+    const double c = (cap > 0.0 && big > cap) ? cap / big : 1.0;
     double* x = P.X[st->cur];
     const float* y = Y + (size_t)i * NOUT;
-    const double u0 = x[i] + sm * dhn * y[0];
-    const double u1 = x[nm + i] + sm * dhn * y[1];
-    const double u2 = x[2 * nm + i] + sm * dhn * y[2];
+    const double u0 = x[i] + c * sm * dhn * y[0];
+    const double u1 = x[nm + i] + c * sm * dhn * y[1];
+    const double u2 = x[2 * nm + i] + c * sm * dhn * y[2];
     const double r = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
     if (r > 0.0 && isfinite(r)) {
         x[i] = u0 / r;
         x[nm + i] = u1 / r;
         x[2 * nm + i] = u2 / r;
     }
-    const double dp = sphi * dhn * y[3];
+    const double dp = c * sphi * dhn * y[3];
     if (isfinite(dp)) P.phi[i] += dp;
 }
 
@@ -540,6 +553,7 @@ struct mm_mlp {
     long long fcap = 0;
     float *F = nullptr, *FY = nullptr;
     mm::Problem* d_prob = nullptr;
+    unsigned* d_max = nullptr;
 };
 
 namespace {
@@ -648,7 +662,8 @@ int mm_mlp_create(mm_mlp** out, int device, uint64_t seed) {
         cudaMalloc(&M->am, NPARAM * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&M->av, NPARAM * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&M->loss, sizeof(float)) != cudaSuccess || cudaMalloc(&M->d_prob, sizeof(mm::Problem)) != cudaSuccess ||
-        cudaMalloc(&M->norm, 2 * NIN * sizeof(float)) != cudaSuccess)
+        cudaMalloc(&M->norm, 2 * NIN * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&M->d_max, sizeof(unsigned)) != cudaSuccess)
         return bail(MM_ERR_OOM);
     {
         float id[2 * NIN];
@@ -687,7 +702,7 @@ void mm_mlp_destroy(mm_mlp* M) {
     for (void* q : {(void*)M->p, (void*)M->norm, (void*)M->wb, (void*)M->g, (void*)M->am, (void*)M->av, (void*)M->loss,
                     (void*)M->X0, (void*)M->A1, (void*)M->A2, (void*)M->A3, (void*)M->DZ1, (void*)M->DZ2,
                     (void*)M->DZ3, (void*)M->DZ4, (void*)M->Yb, (void*)M->part, (void*)M->F, (void*)M->FY,
-                    (void*)M->d_prob})
+                    (void*)M->d_prob, (void*)M->d_max})
         if (q) cudaFree(q);
     if (M->stream) cudaStreamDestroy(M->stream);
     delete M;
@@ -791,7 +806,8 @@ int mm_warmstart_features(mm_ctx* ctx, const double mu0h_next[3], float* X_dev) 
     return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
 }
 
-int mm_warmstart_apply(mm_ctx* ctx, mm_mlp* M, const double mu0h_next[3], double scale_m, double scale_phi) {
+int mm_warmstart_apply(mm_ctx* ctx, mm_mlp* M, const double mu0h_next[3], double scale_m, double scale_phi,
+                       double max_change) {
     mm::CtxView v;
     if (!ctx || !M || !mu0h_next || mm::ctx_view(ctx, &v) != MM_OK) return MM_ERR_ARG;
     if (!v.has_mesh) return mm::ctx_fail(ctx, MM_ERR_STATE, "no mesh uploaded");
@@ -815,7 +831,10 @@ int mm_warmstart_apply(mm_ctx* ctx, mm_mlp* M, const double mu0h_next[3], double
     const double dhn = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     MK(cudaMemcpy(M->d_prob, v.P, sizeof(mm::Problem), cudaMemcpyHostToDevice));
     cudaStream_t st = (cudaStream_t)v.stream;
-    k_apply<<<(v.nm + 255) / 256, 256, 0, st>>>(v.nm, M->d_prob, v.d_state, M->FY, scale_m, scale_phi, dhn);
+    MK(cudaMemsetAsync(M->d_max, 0, sizeof(unsigned), st));
+    k_apply_max<<<(v.nm + 255) / 256, 256, 0, st>>>(v.nm, M->FY, scale_m, dhn, M->d_max);
+    k_apply<<<(v.nm + 255) / 256, 256, 0, st>>>(v.nm, M->d_prob, v.d_state, M->FY, scale_m, scale_phi, dhn,
+                                                max_change, M->d_max);
     MK(cudaGetLastError());
     MK(cudaStreamSynchronize(st));
     return MM_OK;

@@ -17,8 +17,11 @@ mm_warmstart_apply.
 from .api import Params, warmstart_features, warmstart_apply
 
 
-def collect(mag, m0, fields, n_mag, params=None):
-    """Run the curve on `mag` from m0 and return device tensors (X, T, nli)."""
+def collect(mag, m0, fields, n_mag, params=None, max_step_change=0.2):
+    """Run the curve on `mag` from m0 and return device tensors (X, T, nli).
+    Field steps on which some node turned by more than max_step_change
+    (irreversible switching) are left out: the network is to learn the
+    reversible response that keeps the state in its basin, not to jump."""
     import torch
     prm = params or Params()
     mag.set_magnetization(m0)
@@ -32,6 +35,8 @@ def collect(mag, m0, fields, n_mag, params=None):
         X1 = warmstart_features(mag, fields[k + 1], n_mag)
         dh = float(torch.linalg.vector_norm(X[0, 12:15]).item())
         if dh == 0.0:
+            continue
+        if float(torch.linalg.vector_norm(X1[:, 0:3] - X[:, 0:3], dim=1).max().item()) > max_step_change:
             continue
         T = torch.cat([X1[:, 0:3] - X[:, 0:3], X1[:, 15:16] - X[:, 15:16]], dim=1) / dh
         Xs.append(X)
@@ -66,7 +71,7 @@ def train(mlp, X, T, steps=2000, batch=16384, lr=2e-3, seed=0, log_every=0):
     return s_m, s_p, losses
 
 
-def curve(mag, m0, fields, params=None, mlp=None, scales=None):
+def curve(mag, m0, fields, params=None, mlp=None, scales=None, max_change=0.02):
     """Demagnetisation curve; with `mlp`, the warm start is applied before
     every field step after the first.  Returns (stats per step, total nli)."""
     prm = params or Params()
@@ -74,7 +79,7 @@ def curve(mag, m0, fields, params=None, mlp=None, scales=None):
     out = []
     for k, b in enumerate(fields):
         if mlp is not None and k > 0:
-            warmstart_apply(mag, mlp, b, scales[0], scales[1])
+            warmstart_apply(mag, mlp, b, scales[0], scales[1], max_change)
         mag.set_field(b)
         out.append(mag.minimize(prm))
     return out, sum(s["nli"] for s in out)
