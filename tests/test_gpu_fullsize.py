@@ -1,0 +1,93 @@
+"""Parity at the benchmark's full size (80 nm hard-magnet cube, 48^3
+voxels, 857,375 potential unknowns) in the launch configuration bench.py
+times: sampled rows of the potential stiffness against the oracle
+assembled on the sampled nodes' neighbourhoods, closed-form energies of
+uniform states, and the converged first field step against the
+properties of a minimum."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem
+
+pytestmark = pytest.mark.gpu
+
+MU0 = 4e-7 * np.pi
+
+
+@pytest.fixture(scope="module")
+def full():
+    from paper_1801_03690_gb300 import Magnet
+    wl = synth.hard_cube()
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    return wl, mag
+
+
+def test_sizes(full):
+    wl, mag = full
+    s = mag.sizes()
+    assert s["n_mag"] == 49 ** 3
+    assert s["n_phi"] == 95 ** 3
+
+
+def test_sampled_stiffness_rows_match_local_oracle_assembly(full):
+    wl, mag = full
+    mesh = wl.mesh
+    rng = np.random.default_rng(0)
+    v = rng.normal(size=mesh.n_nodes)
+    nx = mesh.shape[0]
+    ijk = lambda n: (n % nx, (n // nx) % nx, n // (nx * nx))
+    boundary = np.zeros(mesh.n_nodes, bool)
+    idx = np.arange(mesh.n_nodes)
+    i, j, k = ijk(idx)
+    boundary[(i == 0) | (j == 0) | (k == 0) | (i == nx - 1) | (j == nx - 1) | (k == nx - 1)] = True
+    out = mag.potential_matvec(v)
+    assert np.all(out[boundary] == 0.0)
+    samples = rng.choice(np.nonzero(~boundary)[0], size=64, replace=False)
+    # tets touching the samples; assemble the oracle on that sub-mesh
+    touch = np.isin(mesh.tets, samples).any(axis=1)
+    sub_tets = mesh.tets[touch]
+    nodes = np.unique(sub_tets)
+    loc = -np.ones(mesh.n_nodes, dtype=np.int64)
+    loc[nodes] = np.arange(nodes.size)
+    P = fem.assemble(mesh.xyz[nodes], loc[sub_tets], mesh.region[touch], wl.materials)
+    vv = np.where(boundary[nodes], 0.0, v[nodes])          # outer-surface values do not enter
+    ref = P.Kfull[loc[samples]] @ vv
+    np.testing.assert_allclose(out[samples], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_uniform_state_energies(full):
+    from paper_1801_03690_gb300 import Params
+    wl, mag = full
+    u = np.array([0.3, -0.4, np.sqrt(1 - 0.25)])
+    b = np.array([0.0, 0.2, -1.0])
+    mag.set_field(b)
+    F, terms = mag.energy(np.tile(u, (wl.mesh.n_nodes, 1)), Params(precision=1, poisson_tol=1e-10))
+    Ms, K = wl.materials[1, 0], wl.materials[1, 2]
+    ax = wl.materials[1, 3:6] / np.linalg.norm(wl.materials[1, 3:6])
+    V = (80e-9) ** 3
+    ex, an, dm, ze = terms
+    assert abs(ex) < 1e-9 * abs(an)                      # uniform m: no exchange energy
+    assert an == pytest.approx(-K * V * (u @ ax) ** 2, rel=1e-10)
+    assert ze == pytest.approx(-Ms * V * (b @ u), rel=1e-10)
+    assert 0.0 < dm < 0.5 * MU0 * Ms ** 2 * V            # 0 < N < 1
+    assert F == pytest.approx(ex + an + dm + ze, rel=1e-12)
+
+
+def test_first_field_step_reaches_a_minimum(full):
+    from paper_1801_03690_gb300 import Params
+    wl, mag = full
+    mag.set_magnetization(wl.m0)
+    mag.set_field(wl.fields[1])
+    F0, _ = mag.energy(wl.m0, Params(precision=1))
+    st = mag.minimize(Params(precision=1))
+    assert st["status"] == "ok"
+    assert st["F"] < F0
+    m = mag.get_magnetization()
+    mag_nodes = np.linalg.norm(m, axis=1) > 0
+    np.testing.assert_allclose(np.linalg.norm(m[mag_nodes], axis=1), 1.0, atol=1e-13)
+    g = mag.gradient(None, projected=True, params=Params(precision=1))
+    # t3 at the returned state (internal units)
+    assert np.abs(g).max() < 1e-10 ** (1 / 3) * (1 + abs(st["F_internal"]))
+    assert st["evals"] == 2 * st["nli"] + 1 + st["ls_extra"]
