@@ -23,6 +23,11 @@ import sys
 import tempfile
 import time
 
+# the CPU oracle legs run on one host core: pin the BLAS / OpenMP pools
+# before numpy is imported so that the reported core count is the real one
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
