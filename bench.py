@@ -241,6 +241,8 @@ def main():
                          "batch: the batched platelet workload")
     ap.add_argument("--n-platelets", type=int, default=64)
     ap.add_argument("--forms", default="plain_fp64,precision,precision_learned")
+    ap.add_argument("--theta-max", type=float, default=0.1,
+                    help="curve mode: line-search cap on the largest nodal step (the paper's reading: 0.1)")
     ap.add_argument("--max-change", type=float, default=0.02,
                     help="warm start: cap on the largest predicted nodal change")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
@@ -446,8 +448,8 @@ def curve_mode(args, rank, local_rank):
                      "statuses": sorted(set(s["status"] for s in sts)),
                      "nli_per_step": [int(s["nli"]) for s in sts], "Mz": M[:, 2].tolist()}
 
-    run("plain_fp64", Params(precision=0))
-    run("precision", Params(precision=1))
+    run("plain_fp64", Params(precision=0, theta_max=args.theta_max))
+    run("precision", Params(precision=1, theta_max=args.theta_max))
     # learned warm start: train on the curve of the same recipe at half the resolution
     if "precision_learned" not in forms:
         if rank == 0:
@@ -466,7 +468,7 @@ def curve_mode(args, rank, local_rank):
     net = MLP(device=local_rank, seed=11)
     s_m, s_p, losses = warmstart.train(net, X, T, steps=1500, batch=16384, lr=2e-3, log_every=500)
     train_s = time.perf_counter() - t0
-    run("precision_learned", Params(precision=1), net=net, scales=(s_m, s_p))
+    run("precision_learned", Params(precision=1, theta_max=args.theta_max), net=net, scales=(s_m, s_p))
     ref = out.get("plain_fp64") or out.get("precision")
     for k in ("precision", "precision_learned"):
         if k not in out or out[k] is ref:

@@ -757,6 +757,8 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     if ((rc = dalloc(ctx, &P.idir[1], v3))) return rc;
     if ((rc = dalloc(ctx, &P.ihd, v3))) return rc;
     if ((rc = dalloc(ctx, &P.phi, nphi))) return rc;
+    for (int s = 0; s < MM_NSLOT; ++s)
+        if ((rc = dalloc(ctx, &P.PHI[s], nphi))) return rc;
     if ((rc = dalloc(ctx, &P.rhs, nm))) return rc;
     if ((rc = dalloc(ctx, &P.pres, nphi))) return rc;
     if ((rc = dalloc(ctx, &P.pprec, nphi))) return rc;
@@ -803,6 +805,7 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     CK_CUDA(z(P.idir[1], v3));
     CK_CUDA(z(P.ihd, v3));
     CK_CUDA(z(P.phi, nphi));
+    for (int s = 0; s < MM_NSLOT; ++s) CK_CUDA(z(P.PHI[s], nphi));
     CK_CUDA(z(P.rhs, nm));
     CK_CUDA(z(P.pres, nphi));
     CK_CUDA(z(P.pprec, nphi));

@@ -103,7 +103,8 @@ struct Problem {
     double* idir[2];         // [3][nm] direction (double buffer)
     double* ihd;             // [3][nm] H * direction
     // potential solve (Algorithm 1 on K_phi)
-    double* phi;             // [nphi]
+    double* phi;             // [nphi] working potential (the last solve)
+    double* PHI[MM_NSLOT];   // [nphi] potential of each state slot
     double* rhs;             // [nm] D m on the magnetic rows (zero elsewhere)
     double* pres;            // [nphi] residual
     double* pprec;           // [nphi] Jacobi-preconditioned residual

@@ -151,6 +151,7 @@ extern "C" int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, cons
     Q.isol = Q.ires = Q.iprec = Q.ihd = S + o_GP;    // not used by an evaluation
     Q.idir[0] = Q.idir[1] = S + o_GP;
     Q.phi = S + o_phi;
+    for (int s = 0; s < MM_NSLOT; ++s) Q.PHI[s] = S + o_phi;   // an evaluation saves phi in place
     Q.rhs = S + o_rhs;
     Q.pres = S + o_res;
     Q.pprec = S + o_prec;

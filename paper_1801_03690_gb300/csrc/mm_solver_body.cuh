@@ -596,6 +596,7 @@ __device__ bool ph_gradient(Ctx& C, int s, bool trial) {
     double mx[1] = {0.0};
     ROWS(p, P.nphi) {
         acc[4] += P.phi[p] * P.pres[p];
+        P.PHI[s][p] = P.phi[p];
         if (p < nm) {
             const int i = p;
             acc[3] += P.phi[i] * P.rhs[i];
@@ -672,8 +673,31 @@ __device__ bool ph_gradient(Ctx& C, int s, bool trial) {
 }
 
 // One function evaluation at slot s: at x_c + a d (trial) or at x_s as is.
-__device__ bool evaluate(Ctx& C, int c, int s, bool trial, double a) {
+// Warm start of a trial evaluation: phi is linear in m and the trial point
+// is x_c + a d to first order, so phi(a) ~ PHI[c] + theta (PHI[ref] - PHI[c])
+// with theta = a / a_ref (theta = 0: start from the current state's phi).
+__device__ bool ph_phi_start(Ctx& C, int c, int ref, double theta) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const double* a = P.PHI[c];
+    const double* b = P.PHI[ref];
+    ROWS(p, P.nphi) P.phi[p] = (theta == 0.0) ? a[p] : a[p] + theta * (b[p] - a[p]);
+    return team_sync(t);
+}
+
+__device__ bool ph_phi_restore(Ctx& C, int c) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    ROWS(p, P.nphi) P.phi[p] = P.PHI[c][p];
+    return team_sync(t);
+}
+
+// One function evaluation at slot s: at x_c + a d (trial, potential warm
+// start from the slots c and ref, see ph_phi_start) or at x_s as is (warm
+// start from the last potential).
+__device__ bool evaluate(Ctx& C, int c, int s, bool trial, double a, int ref = 0, double theta = 0.0) {
     if (trial && !ph_trial(C, c, s, a)) return false;
+    if (trial && !ph_phi_start(C, c, ref, theta)) return false;
     if (!solve_potential(C, s)) return false;
     if (!ph_gradient(C, s, trial)) return false;
     C.evals++;
@@ -941,12 +965,12 @@ __device__ int minimize(Ctx& C, int& cur) {
         const double a_max = prm.theta_max / dmax;
         const double a_t = fmin(a_prev, a_max);
         const int ts = (c + 1) % MM_NSLOT, ss = (c + 2) % MM_NSLOT;
-        if (!evaluate(C, c, ts, true, a_t)) return ST_TIMEOUT;
+        if (!evaluate(C, c, ts, true, a_t, c, 0.0)) return ST_TIMEOUT;
         double a_s;
         if (!cubic_step(F0, dphi0, a_t, C.sl[ts].F, C.sl[ts].dphi, a_s))
             a_s = (C.sl[ts].dphi < 0.0) ? 4.0 * a_t : 0.5 * a_t;
         a_s = fmin(fmax(a_s, 0.1 * a_t), fmin(4.0 * a_t, a_max));
-        if (!evaluate(C, c, ss, true, a_s)) return ST_TIMEOUT;
+        if (!evaluate(C, c, ss, true, a_s, ts, a_s / a_t)) return ST_TIMEOUT;
         int b;
         double a_b;
         if (C.sl[ss].F <= C.sl[ts].F) {
@@ -960,7 +984,7 @@ __device__ int minimize(Ctx& C, int& cur) {
             bool found = false;
             double a = 0.5 * fmin(a_t, a_s);
             for (int k = 0; k < prm.max_backtrack; ++k) {
-                if (!evaluate(C, c, ts, true, a)) return ST_TIMEOUT;
+                if (!evaluate(C, c, ts, true, a, ss, a / a_s)) return ST_TIMEOUT;
                 C.ls_extra++;
                 if (C.sl[ts].F <= F0 + prm.c1 * a * dphi0) {
                     b = ts;
@@ -991,6 +1015,9 @@ __device__ int minimize(Ctx& C, int& cur) {
         if (t1 && t2 && t3) status = ST_OK;
     }
     if (status == ST_RUNNING) status = ST_NOT_CONVERGED;
+    // leave the accepted state's potential as the working one (the next
+    // field step starts from it; the host reads it)
+    if (!ph_phi_restore(C, c)) return ST_TIMEOUT;
     cur = c;
     return status;
 }
