@@ -749,7 +749,6 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     }
     if ((rc = dalloc(ctx, &P.unorm, nm))) return rc;
     if ((rc = dalloc(ctx, &P.d, v3))) return rc;
-    P.yout = nullptr;
     if ((rc = dalloc(ctx, &P.isol, v3))) return rc;
     if ((rc = dalloc(ctx, &P.ires, v3))) return rc;
     if ((rc = dalloc(ctx, &P.iprec, v3))) return rc;

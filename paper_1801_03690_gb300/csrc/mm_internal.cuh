@@ -95,7 +95,6 @@ struct Problem {
     double* LAM[MM_NSLOT];   // [nm] lambda = m . grad F
     double* unorm;           // [nm] |x + a d| of the last trial point
     double* d;               // [3][nm] NCG direction
-    double* yout;            // [3][nm] preconditioner output
     // inner solve (Algorithm 1 on H)
     double* isol;            // [3][nm]
     double* ires;            // [3][nm] residual

@@ -147,7 +147,6 @@ extern "C" int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, cons
     }
     Q.unorm = S + o_un;
     Q.d = S + o_un;                                  // not read by an evaluation
-    Q.yout = nullptr;
     Q.isol = Q.ires = Q.iprec = Q.ihd = S + o_GP;    // not used by an evaluation
     Q.idir[0] = Q.idir[1] = S + o_GP;
     Q.phi = S + o_phi;
