@@ -235,10 +235,11 @@ def main():
     ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "medium", "soft_cube", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch"],
+    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling"],
                     help="steps: the timed field steps (default line); curve: full demagnetisation "
                          "curves of the plain FP64, precision and precision + learned forms; "
-                         "batch: the batched platelet workload")
+                         "batch: the batched platelet workload; scaling: field steps of the hard "
+                         "cube at several resolutions")
     ap.add_argument("--n-platelets", type=int, default=64)
     ap.add_argument("--forms", default="plain_fp64,precision,precision_learned")
     ap.add_argument("--theta-max", type=float, default=0.1,
@@ -280,6 +281,8 @@ def main():
         return curve_mode(args, rank, local_rank)
     if args.mode == "batch":
         return batch_mode(args, rank, local_rank)
+    if args.mode == "scaling":
+        return scaling_mode(args, rank, local_rank)
 
     wl = workload(args.workload)
     fields = wl.fields
@@ -485,6 +488,47 @@ def curve_mode(args, rank, local_rank):
         print(json.dumps({"mode": "curve", "workload": wl.name, "sizes": sz, "n_fields": len(fields),
                           "forms": out}))
     mag.close()
+    return 0
+
+
+def scaling_mode(args, rank, local_rank):
+    """Size sweep at fixed physics (the 80 nm hard cube at several
+    resolutions, air box 2x): NCG iterations and potential CG steps per field
+    step, throughput, achieved bandwidth (precision form, field steps 3-7)."""
+    import torch
+    import synth
+    from paper_1801_03690_gb300 import Magnet, Params
+    prm = Params(precision=1)
+    rows = []
+    for n in (16, 24, 32, 40, 48, 56, 64):
+        wl = synth.hard_cube(n_mag=n)
+        mag = Magnet(device=local_rank)
+        mag.upload_workload(wl)
+        sz = mag.sizes()
+        mag.set_magnetization(wl.m0)
+        for k in range(3):
+            mag.set_field(wl.fields[k])
+            mag.minimize(prm)
+        torch.cuda.synchronize()
+        nli = mi = ev = 0
+        nbytes, kms = 0, 0.0
+        t0 = time.perf_counter()
+        for k in range(3, 8):
+            mag.set_field(wl.fields[k])
+            mag.minimize_async(prm)
+            st = mag.get_stats()
+            kms += mag.last_kernel_ms()
+            nbytes += alg_bytes(st, sz)
+            nli += st["nli"]
+            mi += st["mi"]
+            ev += st["evals"]
+        dt = time.perf_counter() - t0
+        rows.append({"n_mag_voxels": n, "n_mag": sz["n_mag"], "n_phi": sz["n_phi"],
+                     "nli_per_step": nli / 5, "cg_steps_per_eval": mi / ev, "NCG_it_per_s": nli / dt,
+                     "ms_per_step": 1000 * dt / 5, "achieved_GBs": nbytes / (kms / 1000) / 1e9})
+        mag.close()
+    if rank == 0:
+        print(json.dumps({"mode": "scaling", "workload": "hard_cube (80 nm, box 2x)", "rows": rows}))
     return 0
 
 
