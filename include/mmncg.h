@@ -91,6 +91,11 @@ typedef struct {
                            /* updates") until poisson_tol                          */
     double inner_tol;      /* FP32 residual drop that triggers an FP64 update (0.1)*/
     int max_refine;        /* cap on FP64 updates per potential solve (64)         */
+    int amg;               /* precision form: 1 = precondition the FP32 solve with */
+                           /* a smoothed-aggregation multigrid V-cycle (Sec. 3.1  */
+                           /* uses algebraic multigrid there), 0 = Jacobi (0).    */
+                           /* Needs the hierarchy mm_upload_mesh builds when      */
+                           /* n_phi exceeds the dense coarse size; else Jacobi.   */
 } mm_params;
 
 /* Counters of one call, in the columns of Table 1 plus the energy. */
@@ -133,6 +138,13 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz,
 /* Sizes: magnetic nodes, potential unknowns, nonzeros of the two graphs. */
 int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi,
              int64_t* nnz_mag, int64_t* nnz_phi);
+
+/* Multigrid hierarchy of the potential solve built by mm_upload_mesh
+ * (Sec. 3.1 preconditions that solve with algebraic multigrid): *n_levels
+ * smoothed levels (0: none, mm_params.amg then falls back to Jacobi) and
+ * rows[0..n_levels] the rows of every level, the last the coarsest (solved
+ * with a dense inverse).  rows may be NULL; at most max_rows are written. */
+int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int32_t max_rows);
 
 /* Magnetisation per node ([n_nodes][3]); normalised on entry (N m, Eq. opt2). */
 int mm_set_magnetization(mm_ctx* ctx, const double* m);

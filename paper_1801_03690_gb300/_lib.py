@@ -35,7 +35,7 @@ class mm_params(C.Structure):
                 ("theta_max", C.c_double), ("c1", C.c_double), ("max_backtrack", C.c_int),
                 ("keep_last_term", C.c_int), ("poisson_tol", C.c_double),
                 ("poisson_max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int)]
+                ("max_refine", C.c_int), ("amg", C.c_int)]
 
 
 class mm_stats(C.Structure):
@@ -54,6 +54,7 @@ EXPORTS = {
     "mm_upload_mesh": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                  C.c_void_p, C.c_int32, C.POINTER(mm_material)]),
     "mm_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int64)] * 4),
+    "mm_amg_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_int32]),
     "mm_set_magnetization": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mm_get_magnetization": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mm_set_magnetization_dev": (C.c_int, [C.c_void_p, C.c_void_p]),

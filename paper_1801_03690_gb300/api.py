@@ -34,6 +34,7 @@ class Params:
     precision: int = 0           # 1 = FP32 potential solve with FP64 refinement
     inner_tol: float = 0.1
     max_refine: int = 64
+    amg: int = 0                 # 1 = multigrid-preconditioned FP32 solve
 
     def to_c(self):
         p = L.mm_params()
@@ -117,6 +118,14 @@ class Magnet:
         v = [C.c_int64() for _ in range(4)]
         self._check(self._lib.mm_sizes(self._h, *[C.byref(x) for x in v]))
         return {"n_mag": v[0].value, "n_phi": v[1].value, "nnz_mag": v[2].value, "nnz_phi": v[3].value}
+
+    def amg_levels(self):
+        """Rows of every level of the potential solve's multigrid hierarchy,
+        finest first, coarsest (dense) last; [] when there is none."""
+        n = C.c_int32()
+        rows = (C.c_int64 * (64))()
+        self._check(self._lib.mm_amg_info(self._h, C.byref(n), rows, 64))
+        return [int(rows[l]) for l in range(n.value + 1)] if n.value > 0 else []
 
     # ----------------------------------------------------------------- state
     def set_magnetization(self, m):

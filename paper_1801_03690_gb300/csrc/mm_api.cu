@@ -178,6 +178,7 @@ mm::Params to_params(const mm_params* p) {
     q.poisson_tol = p->poisson_tol;
     q.poisson_max_iter = p->poisson_max_iter;
     q.precision = p->precision;
+    q.amg = p->amg;
     q.inner_tol = p->inner_tol;
     q.max_refine = p->max_refine;
     return q;
@@ -197,6 +198,7 @@ int check_params(mm_ctx* ctx, const mm_params* p) {
     if (p->precision == 1 && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
         return fail(ctx, MM_ERR_ARG, "inner_tol must be in (0, 1)");
     if (p->precision == 1 && p->max_refine < 1) return fail(ctx, MM_ERR_ARG, "max_refine must be >= 1");
+    if (p->amg != 0 && p->amg != 1) return fail(ctx, MM_ERR_ARG, "amg must be 0 or 1");
     return MM_OK;
 }
 
@@ -231,11 +233,360 @@ void build_sell(const std::vector<std::vector<int>>& rows, std::vector<long long
     }
 }
 
+// CSR matrix on the host.
+struct HostCsr {
+    int n = 0;                  // rows
+    int m = 0;                  // columns
+    std::vector<long long> ptr;
+    std::vector<int> col;
+    std::vector<double> val;
+};
+
+// Greedy aggregation of the matrix graph: (1) a node whose neighbours are
+// all free starts an aggregate with them; (2) remaining nodes join the
+// aggregate of their first aggregated neighbour; (3) the rest become
+// singletons.  Returns the number of aggregates.
+int aggregate(const HostCsr& A, std::vector<int>& agg) {
+    const int n = A.n;
+    agg.assign(n, -1);
+    int na = 0;
+    for (int i = 0; i < n; ++i) {
+        if (agg[i] >= 0) continue;
+        bool free_nb = true;
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1] && free_nb; ++e)
+            if (A.col[e] != i && A.val[e] != 0.0 && agg[A.col[e]] >= 0) free_nb = false;
+        if (!free_nb) continue;
+        agg[i] = na;
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
+            if (A.val[e] != 0.0) agg[A.col[e]] = na;
+        ++na;
+    }
+    std::vector<int> first(agg);
+    for (int i = 0; i < n; ++i) {
+        if (first[i] >= 0) continue;
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+            const int j = A.col[e];
+            if (j != i && A.val[e] != 0.0 && first[j] >= 0) {
+                agg[i] = first[j];
+                break;
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (agg[i] < 0) agg[i] = na++;
+    return na;
+}
+
+// C = A B (sparse, dense accumulator over the columns of B; entries that
+// cancel exactly are kept, columns in first-touch order).
+HostCsr spgemm(const HostCsr& A, const HostCsr& B) {
+    HostCsr C;
+    C.n = A.n;
+    C.m = B.m;
+    C.ptr.assign(A.n + 1, 0);
+    std::vector<double> acc(B.m, 0.0);
+    std::vector<int> mark(B.m, -1), cols;
+    for (int i = 0; i < A.n; ++i) {
+        cols.clear();
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+            const int k = A.col[e];
+            const double a = A.val[e];
+            for (long long f = B.ptr[k]; f < B.ptr[k + 1]; ++f) {
+                const int j = B.col[f];
+                if (mark[j] != i) {
+                    mark[j] = i;
+                    acc[j] = 0.0;
+                    cols.push_back(j);
+                }
+                acc[j] += a * B.val[f];
+            }
+        }
+        for (int j : cols) {
+            C.col.push_back(j);
+            C.val.push_back(acc[j]);
+        }
+        C.ptr[i + 1] = (long long)C.col.size();
+    }
+    return C;
+}
+
+HostCsr transpose(const HostCsr& A) {
+    HostCsr T;
+    T.n = A.m;
+    T.m = A.n;
+    T.ptr.assign(A.m + 1, 0);
+    for (int c : A.col) T.ptr[c + 1]++;
+    for (int j = 0; j < A.m; ++j) T.ptr[j + 1] += T.ptr[j];
+    T.col.resize(A.col.size());
+    T.val.resize(A.val.size());
+    std::vector<long long> fill(T.ptr.begin(), T.ptr.end() - 1);
+    for (int i = 0; i < A.n; ++i)
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+            const long long f = fill[A.col[e]]++;
+            T.col[f] = i;
+            T.val[f] = A.val[e];
+        }
+    return T;
+}
+
+// B - s D A for a diagonal D (row scaling), B and A of the same shape.
+HostCsr minus_scaled_rows(const HostCsr& B, double s, const std::vector<double>& D, const HostCsr& A) {
+    HostCsr C;
+    C.n = B.n;
+    C.m = B.m;
+    C.ptr.assign(B.n + 1, 0);
+    std::vector<double> acc(B.m, 0.0);
+    std::vector<int> mark(B.m, -1), cols;
+    for (int i = 0; i < B.n; ++i) {
+        cols.clear();
+        auto add = [&](int j, double v) {
+            if (mark[j] != i) {
+                mark[j] = i;
+                acc[j] = 0.0;
+                cols.push_back(j);
+            }
+            acc[j] += v;
+        };
+        for (long long e = B.ptr[i]; e < B.ptr[i + 1]; ++e) add(B.col[e], B.val[e]);
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) add(A.col[e], -s * D[i] * A.val[e]);
+        for (int j : cols) {
+            C.col.push_back(j);
+            C.val.push_back(acc[j]);
+        }
+        C.ptr[i + 1] = (long long)C.col.size();
+    }
+    return C;
+}
+
+// SELL-32 layout of a host CSR (values as float); padding entries carry
+// value 0 and their own row as column where that is a column of A, else 0.
+void csr_to_sell(const HostCsr& A, std::vector<long long>& sptr, std::vector<int>& col, std::vector<float>& val) {
+    const long long n = A.n, ns = (n + 31) / 32;
+    sptr.assign(ns + 1, 0);
+    for (long long s = 0; s < ns; ++s) {
+        long long w = 0;
+        for (long long r = s * 32; r < std::min(n, s * 32 + 32); ++r) w = std::max(w, A.ptr[r + 1] - A.ptr[r]);
+        sptr[s + 1] = sptr[s] + 32 * w;
+    }
+    col.assign(sptr[ns], 0);
+    val.assign(sptr[ns], 0.0f);
+    for (long long s = 0; s < ns; ++s) {
+        const long long w = (sptr[s + 1] - sptr[s]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const long long r = s * 32 + l;
+            for (long long k = 0; k < w; ++k) {
+                const long long e = sptr[s] + 32 * k + l;
+                if (r < n && k < A.ptr[r + 1] - A.ptr[r]) {
+                    col[e] = A.col[A.ptr[r] + k];
+                    val[e] = (float)A.val[A.ptr[r] + k];
+                } else {
+                    col[e] = (r < A.m) ? (int)r : 0;   // padding: a valid column, value 0
+                }
+            }
+        }
+    }
+}
+
+// Inverse of a small SPD matrix, FP64, returned row-major in FP32:
+// A = L L^T (Cholesky), L^-1 row by row, A^-1 = L^-T L^-1.  All inner loops
+// run along rows.  Returns false if A is not numerically positive definite.
+bool dense_inverse(const HostCsr& A, std::vector<float>& inv) {
+    const int n = A.n;
+    std::vector<double> L((size_t)n * n, 0.0), Li((size_t)n * n, 0.0), acc(n);
+    for (int i = 0; i < n; ++i)
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) L[(size_t)i * n + A.col[e]] += A.val[e];
+    for (int j = 0; j < n; ++j) {
+        double* Lj = &L[(size_t)j * n];
+        double d = Lj[j];
+        for (int k = 0; k < j; ++k) d -= Lj[k] * Lj[k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        Lj[j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double* Lr = &L[(size_t)i * n];
+            double v = Lr[j];
+            for (int k = 0; k < j; ++k) v -= Lr[k] * Lj[k];
+            Lr[j] = v / d;
+        }
+    }
+    for (int i = 0; i < n; ++i) {                   // row i of L^-1
+        const double* Lr = &L[(size_t)i * n];
+        std::fill(acc.begin(), acc.begin() + i, 0.0);
+        for (int k = 0; k < i; ++k) {
+            const double c = Lr[k];
+            const double* Lk = &Li[(size_t)k * n];
+            for (int j = 0; j <= k; ++j) acc[j] += c * Lk[j];
+        }
+        double* out = &Li[(size_t)i * n];
+        const double di = 1.0 / Lr[i];
+        for (int j = 0; j < i; ++j) out[j] = -acc[j] * di;
+        out[i] = di;
+    }
+    std::vector<double> X((size_t)n * n, 0.0);
+    for (int k = 0; k < n; ++k) {                   // X += row_k^T row_k
+        const double* Lk = &Li[(size_t)k * n];
+        for (int i = 0; i <= k; ++i) {
+            const double c = Lk[i];
+            double* Xi = &X[(size_t)i * n];
+            for (int j = 0; j <= k; ++j) Xi[j] += c * Lk[j];
+        }
+    }
+    inv.resize((size_t)n * n);
+    for (size_t e = 0; e < inv.size(); ++e) inv[e] = (float)X[e];
+    return true;
+}
+
 template <class T>
 int upload(mm_ctx* ctx, T** dst, const T* src, size_t count) {
     int rc = dalloc(ctx, dst, count);
     if (rc) return rc;
     if (count) CK_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return MM_OK;
+}
+
+// Upload a host CSR matrix in SELL-32 form with FP32 values.
+int upload_sell(mm_ctx* ctx, const HostCsr& A, const long long** sptr, const int** col, const float** val) {
+    std::vector<long long> sp;
+    std::vector<int> c;
+    std::vector<float> v;
+    csr_to_sell(A, sp, c, v);
+    long long* dsp;
+    int* dc;
+    float* dv;
+    int rc;
+    if ((rc = upload(ctx, &dsp, sp.data(), sp.size()))) return rc;
+    if ((rc = upload(ctx, &dc, c.data(), c.size()))) return rc;
+    if ((rc = upload(ctx, &dv, v.data(), v.size()))) return rc;
+    *sptr = dsp;
+    *col = dc;
+    *val = dv;
+    return 0;
+}
+
+constexpr int kCoarseDense = 1536;      // coarsest level solved by a dense inverse
+constexpr double kAmgOmega = 0.8;       // Jacobi damping of the multigrid smoother
+
+// Smoothed-aggregation multigrid hierarchy of K_phi, built on the host in
+// FP64 from the device SELL layout of level 0 (sptr/col/Kp).  Per level:
+// greedy aggregates, tentative prolongation P_t (piecewise constant),
+// P = (I - w_p D^-1 A) P_t with w_p = 4 / (3 rho), rho <= the Gershgorin
+// bound of D^-1 A, the Galerkin operator P^T A P, and the smoothed
+// prolongation U = P - omega D^-1 A P used by the V-cycle with its
+// transpose.  Leaves P.nlev = 0 (Jacobi only) when K_phi is small or the
+// coarsening stalls before the dense size.
+int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& sptr, const std::vector<int>& col,
+                    const double* Kp, long long nnz) {
+    int rc;
+    P.nlev = 0;
+    P.nco = 0;
+    P.amg_omega = (float)kAmgOmega;
+    const int n0 = P.nphi;
+    if (n0 <= kCoarseDense) return MM_OK;
+    HostCsr A;
+    A.n = A.m = n0;
+    A.ptr.assign(n0 + 1, 0);
+    {
+        std::vector<double> kp(nnz);
+        CK_CUDA(cudaStreamSynchronize(ctx->stream));
+        CK_CUDA(cudaMemcpy(kp.data(), Kp, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < n0; ++r) {
+            const long long s = r / 32, w = (sptr[s + 1] - sptr[s]) / 32;
+            for (long long k = 0; k < w; ++k) {
+                const long long e = sptr[s] + 32 * k + (r % 32);
+                if (kp[e] == 0.0) continue;               // SELL padding
+                A.col.push_back(col[e]);
+                A.val.push_back(kp[e]);
+            }
+            A.ptr[r + 1] = (long long)A.col.size();
+        }
+    }
+    struct Host {
+        HostCsr U, Ut;
+        std::vector<float> dinv;
+    };
+    std::vector<Host> host;
+    std::vector<HostCsr> ops;                             // A_l for l >= 1
+    while ((int)host.size() < MM_MAXLEV && A.n > kCoarseDense) {
+        std::vector<int> agg;
+        const int nc = aggregate(A, agg);
+        if (nc > A.n / 2) break;                          // coarsening stalled
+        std::vector<double> dinv(A.n, 1.0);
+        double rho = 0.0;
+        for (int i = 0; i < A.n; ++i) {
+            double d = 0.0, off = 0.0;
+            for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+                if (A.col[e] == i) d = A.val[e];
+                off += std::fabs(A.val[e]);
+            }
+            if (d > 0.0) {
+                dinv[i] = 1.0 / d;
+                rho = std::max(rho, off / d);
+            }
+        }
+        HostCsr Pt;
+        Pt.n = A.n;
+        Pt.m = nc;
+        Pt.ptr.resize(A.n + 1);
+        Pt.col = agg;
+        Pt.val.assign(A.n, 1.0);
+        for (int i = 0; i <= A.n; ++i) Pt.ptr[i] = i;
+        HostCsr Pm = minus_scaled_rows(Pt, 4.0 / (3.0 * rho), dinv, spgemm(A, Pt));
+        HostCsr AP = spgemm(A, Pm);
+        HostCsr Cc = spgemm(transpose(Pm), AP);
+        Host h;
+        h.U = minus_scaled_rows(Pm, kAmgOmega, dinv, AP);
+        h.Ut = transpose(h.U);
+        h.dinv.assign(dinv.begin(), dinv.end());
+        host.push_back(std::move(h));
+        A = std::move(Cc);
+        ops.push_back(A);
+    }
+    std::vector<float> ainv;
+    if (host.empty() || A.n > kCoarseDense || !dense_inverse(A, ainv)) return MM_OK;   // Jacobi only
+    const int L = (int)host.size();
+    for (int l = 0; l < L; ++l) {
+        mm::Level& V = P.lev[l];
+        const Host& h = host[l];
+        V.n = h.U.n;
+        V.nc = h.U.m;
+        if (l == 0) {
+            V.sptr = P.p_sptr;
+            V.col = P.p_col;
+            V.val = P.Kp32;
+            V.dinv = P.dinvP32;
+            V.b = P.pres32;
+            V.y = P.pprec32;
+        } else {
+            if ((rc = upload_sell(ctx, ops[l - 1], &V.sptr, &V.col, &V.val))) return rc;
+            float* d;
+            if ((rc = upload(ctx, &d, h.dinv.data(), h.dinv.size()))) return rc;
+            V.dinv = d;
+            if ((rc = dalloc(ctx, &V.b, V.n))) return rc;
+            if ((rc = dalloc(ctx, &V.y, V.n))) return rc;
+        }
+        if ((rc = upload_sell(ctx, h.U, &V.u_sptr, &V.u_col, &V.u_val))) return rc;
+        {
+            std::vector<float> tv(h.Ut.val.begin(), h.Ut.val.end());
+            long long* tp;
+            int* tc;
+            float* tvd;
+            if ((rc = upload(ctx, &tp, h.Ut.ptr.data(), h.Ut.ptr.size()))) return rc;
+            if ((rc = upload(ctx, &tc, h.Ut.col.data(), h.Ut.col.size()))) return rc;
+            if ((rc = upload(ctx, &tvd, tv.data(), tv.size()))) return rc;
+            V.t_ptr = tp;
+            V.t_col = tc;
+            V.t_val = tvd;
+        }
+        if ((rc = dalloc(ctx, &V.x, V.n))) return rc;
+        if ((rc = dalloc(ctx, &V.rpre, V.n))) return rc;
+    }
+    float* a;
+    if ((rc = upload(ctx, &a, ainv.data(), ainv.size()))) return rc;
+    P.ainv = a;
+    P.nco = A.n;
+    if ((rc = dalloc(ctx, &P.bco, A.n))) return rc;
+    if ((rc = dalloc(ctx, &P.yco, A.n))) return rc;
+    P.nlev = L;
     return MM_OK;
 }
 
@@ -412,6 +763,7 @@ void mm_default_params(mm_params* p) {
     p->precision = 0;
     p->inner_tol = 0.1;
     p->max_refine = 64;
+    p->amg = 0;
 }
 
 int mm_create(mm_ctx** out, const mm_options* opt) {
@@ -781,6 +1133,8 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
         for (float* f : {P.pres32, P.pprec32, P.pdir32, P.pq32, P.pdelta32})
             CK_CUDA(cudaMemsetAsync(f, 0, nphi * sizeof(float), ctx->stream));
     }
+    // aggregation multigrid hierarchy of K_phi for the FP32 potential solve
+    if ((rc = build_hierarchy(ctx, P, p_sptr, p_col, Kp, nnzp))) return rc;
     if ((rc = dalloc(ctx, &P.partials, 2 * (size_t)MM_MAXRED * ctx->blocks))) return rc;
     if ((rc = dalloc(ctx, &P.bar, 64))) return rc;
     if ((rc = dalloc(ctx, &P.err, 1))) return rc;
@@ -838,6 +1192,15 @@ int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi, int64_t* nnz_mag
     if (n_phi) *n_phi = ctx->nphi;
     if (nnz_mag) *nnz_mag = ctx->nnzm_true;
     if (nnz_phi) *nnz_phi = ctx->nnzp_true;
+    return MM_OK;
+}
+
+int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int32_t max_rows) {
+    if (!ctx || !ctx->has_mesh) return MM_ERR_STATE;
+    const mm::Problem& P = ctx->P;
+    if (n_levels) *n_levels = P.nlev;
+    if (rows)
+        for (int l = 0; l <= P.nlev && l < max_rows; ++l) rows[l] = (l < P.nlev) ? P.lev[l].n : P.nco;
     return MM_OK;
 }
 

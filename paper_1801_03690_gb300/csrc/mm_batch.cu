@@ -98,6 +98,7 @@ mm::Params conv(const mm_params* p) {
     q.precision = p->precision;
     q.inner_tol = p->inner_tol;
     q.max_refine = p->max_refine;
+    q.amg = p->amg;
     return q;
 }
 

@@ -18,6 +18,7 @@
 #define MM_SELL 32
 #define MM_MAXRED 16          // reduction values per phase
 #define MM_NSLOT 3            // state slots: current, trial t, trial s
+#define MM_MAXLEV 6           // smoothed levels of the potential preconditioner
 
 namespace mm {
 
@@ -49,6 +50,7 @@ struct Params {
     double poisson_tol;
     int poisson_max_iter;
     int precision;           // 0 = FP64, 1 = FP32 potential solve + FP64 refinement
+    int amg;                 // 1 = aggregation multigrid preconditioner in the FP32 solve
     double inner_tol;        // FP32 solve: relative residual reduction per refinement
     int max_refine;          // FP64 refinement steps per potential solve
 };
@@ -65,6 +67,34 @@ struct DevState {
     double h[3];             // reduced applied field
     int y_is_g;              // 1 if the last preconditioner output is g itself
     int pad;
+};
+
+// Level l of the smoothed-aggregation multigrid preconditioner of the FP32
+// potential solve (level 0: K_phi itself; level l+1: the Galerkin operator
+// P^T A_l P of the smoothed prolongation P of the aggregates of level l).
+// With x = omega D^-1 b (one damped-Jacobi step from zero), the V-cycle is
+//   down: rpre = b - A x,   b_{l+1} = U^T b
+//   up:   y = omega D^-1 (b + rpre) + U y_{l+1}
+// with U = P - omega D^-1 A P, i.e. pre-smoothing, restriction of the
+// residual, coarse correction and post-smoothing with the same damped
+// Jacobi step: a symmetric operator.  Operators are FP32, SELL-32 except U^T.
+struct Level {
+    int n;                   // rows of this level
+    int nc;                  // rows of the next coarser level
+    const long long* sptr;   // A_l (level 0: the FP32 copy of K_phi)
+    const int* col;
+    const float* val;
+    const long long* u_sptr; // U (n rows, nc columns)
+    const int* u_col;
+    const float* u_val;
+    const long long* t_ptr;  // U^T (nc rows, n columns) in CSR: its rows are wide
+    const int* t_col;        // (the support of a smoothed aggregate), one warp
+    const float* t_val;      // takes one row
+    const float* dinv;       // 1 / diag(A_l)
+    float* b;                // right-hand side (level 0: the FP32 residual)
+    float* x;                // omega D^-1 b
+    float* rpre;             // b - A x
+    float* y;                // output (level 0: the preconditioned residual)
 };
 
 struct Problem {
@@ -117,6 +147,14 @@ struct Problem {
     float* pdir32;
     float* pq32;
     float* pdelta32;         // [nphi] correction
+    // smoothed-aggregation multigrid (precision form)
+    int nlev;                // smoothed levels (0: no hierarchy)
+    int nco;                 // rows of the coarsest level (solved densely)
+    Level lev[MM_MAXLEV];
+    const float* ainv;       // [nco][nco] inverse of the coarsest operator
+    float* bco;              // [nco] coarsest right-hand side
+    float* yco;              // [nco] coarsest solution
+    float amg_omega;         // Jacobi damping of the smoother
     // team machinery
     double* partials;        // [2][MM_MAXRED][nblocks]
     unsigned* bar;           // [0] = arrival count, [32] = generation

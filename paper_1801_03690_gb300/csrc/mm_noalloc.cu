@@ -174,6 +174,8 @@ extern "C" int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, cons
     Q.prm.precision = 0;                            // the FP64 evaluation only
     Q.prm.inner_tol = p->inner_tol;
     Q.prm.max_refine = p->max_refine;
+    Q.prm.amg = 0;
+    Q.nlev = 0;
     Q.pres32 = Q.pprec32 = Q.pdir32 = Q.pq32 = Q.pdelta32 = nullptr;
 
     const double hs = 1.0 / (kMu0 * v.Mref);

@@ -220,9 +220,11 @@ __device__ __forceinline__ Row sell_row(const long long* sptr, int r) {
 // chunk are loaded (read-only path) before any gather, so each thread keeps
 // a whole row's worth of independent loads in flight: measured on GB300 this
 // lifts an FP32 SpMV from 3.8 to 6.6 TB/s inside the persistent kernel.
+// Lanes past the row's width read x[pad] (pad = r for square matrices, 0
+// for rectangular ones whose row index may exceed the columns).
 template <int CH, typename T, typename VT, typename XT>
 __device__ __forceinline__ T sell_dot(const long long* __restrict__ sptr, const int* __restrict__ col,
-                                      const VT* __restrict__ val, const XT* x, int r) {
+                                      const VT* __restrict__ val, const XT* x, int r, int pad) {
     const Row A = sell_row(sptr, r);
     T s = T(0);
     for (int k0 = 0; k0 < A.width; k0 += CH) {
@@ -232,13 +234,19 @@ __device__ __forceinline__ T sell_dot(const long long* __restrict__ sptr, const 
         for (int u = 0; u < CH; ++u) {
             const bool ok = k0 + u < A.width;
             const long long e = A.base + 32ll * (k0 + u);
-            c[u] = ok ? __ldg(col + e) : r;
+            c[u] = ok ? __ldg(col + e) : pad;
             v[u] = ok ? __ldg(val + e) : VT(0);
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u) s += (T)v[u] * (T)x[c[u]];
     }
     return s;
+}
+
+template <int CH, typename T, typename VT, typename XT>
+__device__ __forceinline__ T sell_dot(const long long* __restrict__ sptr, const int* __restrict__ col,
+                                      const VT* __restrict__ val, const XT* x, int r) {
+    return sell_dot<CH, T>(sptr, col, val, x, r, r);
 }
 
 // Same for a scalar matrix applied to a SoA 3-vector (stride n).
@@ -423,10 +431,123 @@ __device__ bool ph_pzero(Ctx& C) {
 // operator, vectors and products; FP64 reductions); then phi += delta and
 // r -= K delta in FP64 (iterative refinement of the FP64 residual).
 
-// r32 = r, z32 = diag^-1 r32, delta = 0.  Sums: r.z, |r|^2.
+// One warp's dot product of a CSR row with x (lanes stride the row, four
+// independent loads in flight per lane; fixed summation order).
+__device__ __forceinline__ float warp_csr_dot(const long long* __restrict__ ptr, const int* __restrict__ col,
+                                              const float* __restrict__ val, const float* x, int row,
+                                              int lane) {
+    const long long e = ptr[row + 1];
+    long long k = ptr[row] + lane;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    for (; k + 96 < e; k += 128) {
+        const int c0 = __ldg(col + k), c1 = __ldg(col + k + 32), c2 = __ldg(col + k + 64),
+                  c3 = __ldg(col + k + 96);
+        const float v0 = __ldg(val + k), v1 = __ldg(val + k + 32), v2 = __ldg(val + k + 64),
+                    v3 = __ldg(val + k + 96);
+        s0 += v0 * x[c0];
+        s1 += v1 * x[c1];
+        s2 += v2 * x[c2];
+        s3 += v3 * x[c3];
+    }
+    for (; k < e; k += 32) s0 += __ldg(val + k) * x[__ldg(col + k)];
+    return warp_sum_t<float>((s0 + s1) + (s2 + s3));
+}
+
+// ---- smoothed-aggregation multigrid V-cycle (the FP32 solve's
+// preconditioner when a hierarchy exists and prm.amg is set); operators as
+// in struct Level.  Down phase of level l: rpre = b - A x on its rows (one
+// thread per row) and b_{l+1} = U^T b, x_{l+1} = omega D^-1 b_{l+1} on the
+// rows of level l+1 (one warp per row).
+__device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const Level& V = P.lev[l];
+    const bool last = (l + 1 == P.nlev);
+    float* bn = last ? P.bco : P.lev[l + 1].b;
+    float* xn = last ? nullptr : P.lev[l + 1].x;
+    const float* dn = last ? nullptr : P.lev[l + 1].dinv;
+    const float* b = V.b;
+    ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<8, float>(V.sptr, V.col, V.val, V.x, r);
+    const int lane = threadIdx.x & 31, wpb = MM_BLOCK / 32;
+    for (int I = t.rank * wpb + (int)(threadIdx.x >> 5); I < V.nc; I += t.nb * wpb) {
+        const float s = warp_csr_dot(V.t_ptr, V.t_col, V.t_val, b, I, lane);
+        if (lane == 0) {
+            bn[I] = s;
+            if (!last) xn[I] = P.amg_omega * dn[I] * s;
+        }
+    }
+    return team_sync(t);
+}
+
+// Coarsest level: y = A_c^-1 b, one warp per row of the dense inverse.
+__device__ __noinline__ bool ph_amg_dense(Ctx& C) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int n = P.nco, lane = threadIdx.x & 31;
+    const int wpb = MM_BLOCK / 32;
+    for (int row = t.rank * wpb + (int)(threadIdx.x >> 5); row < n; row += t.nb * wpb) {
+        const float* a = P.ainv + (size_t)row * n;
+        float s = 0.0f;
+        for (int j = lane; j < n; j += 32) s += a[j] * P.bco[j];
+        s = warp_sum_t<float>(s);
+        if (lane == 0) P.yco[row] = s;
+    }
+    return team_sync(t);
+}
+
+// Up phase of level l: y = omega D^-1 (b + rpre) + U y_{l+1}.  At level 0,
+// y is the preconditioned residual z; sums r.z and |r|^2.
+__device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const Level& V = P.lev[l];
+    const float* yc = (l + 1 == P.nlev) ? P.yco : P.lev[l + 1].y;
+    float acc[2] = {0.0f, 0.0f};
+    ROWS(r, V.n) {
+        const float s = sell_dot<8, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0);
+        const float b = V.b[r];
+        const float y = P.amg_omega * V.dinv[r] * (b + V.rpre[r]) + s;
+        V.y[r] = y;
+        acc[0] += b * y;
+        acc[1] += b * b;
+    }
+    if (l > 0) return team_sync(t);
+    double out[2];
+    if (!team_sum_f32<2>(t, acc, out)) return false;
+    rz = out[0];
+    rr = out[1];
+    return true;
+}
+
+// z = V-cycle(r) for r = pres32, whose smoothed iterate amg_x0 = omega
+// D^-1 r has been written (and a barrier passed) by the caller.
+__device__ bool amg_vcycle(Ctx& C, double& rz, double& rr) {
+    const Problem& P = *C.P;
+    for (int l = 0; l < P.nlev; ++l)
+        if (!ph_amg_down(C, l)) return false;
+    if (!ph_amg_dense(C)) return false;
+    for (int l = P.nlev - 1; l >= 0; --l)
+        if (!ph_amg_up(C, l, rz, rr)) return false;
+    return true;
+}
+
+__device__ __forceinline__ bool use_amg(const Problem& P) { return P.prm.amg != 0 && P.nlev > 0; }
+
+// r32 = r, z32 = M^-1 r32 (Jacobi or the V-cycle), delta = 0.  Sums: r.z, |r|^2.
 __device__ bool ph_p32_init(Ctx& C, double& rz, double& rr) {
     const Problem& P = *C.P;
     Team& t = C.t;
+    if (use_amg(P)) {
+        float* x0 = P.lev[0].x;
+        ROWS(p, P.nphi) {
+            const float r = (float)P.pres[p];
+            P.pres32[p] = r;
+            x0[p] = P.amg_omega * P.dinvP32[p] * r;
+            P.pdelta32[p] = 0.0f;
+        }
+        if (!team_sync(t)) return false;
+        return amg_vcycle(C, rz, rr);
+    }
     float acc[2] = {0.0f, 0.0f};
     double out[2];
     ROWS(p, P.nphi) {
@@ -465,10 +586,21 @@ __device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
     return true;
 }
 
-// delta += a d; r -= a q; z = diag^-1 r.  Sums: r.z, |r|^2.
+// delta += a d; r -= a q; z = M^-1 r.  Sums: r.z, |r|^2.
 __device__ bool ph_p32_update(Ctx& C, float a, double& rz, double& rr) {
     const Problem& P = *C.P;
     Team& t = C.t;
+    if (use_amg(P)) {
+        float* x0 = P.lev[0].x;
+        ROWS(p, P.nphi) {
+            P.pdelta32[p] += a * P.pdir32[p];
+            const float r = P.pres32[p] - a * P.pq32[p];
+            P.pres32[p] = r;
+            x0[p] = P.amg_omega * P.dinvP32[p] * r;
+        }
+        if (!team_sync(t)) return false;
+        return amg_vcycle(C, rz, rr);
+    }
     float acc[2] = {0.0f, 0.0f};
     double out[2];
     ROWS(p, P.nphi) {
