@@ -554,7 +554,8 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
             V.col = P.p_col;
             V.val = P.Kp32;
             V.dinv = P.dinvP32;
-            V.b = P.pres32;
+            V.b = nullptr;
+            V.x = nullptr;
             V.y = P.pprec32;
         } else {
             if ((rc = upload_sell(ctx, ops[l - 1], &V.sptr, &V.col, &V.val))) return rc;
@@ -577,9 +578,10 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
             V.t_col = tc;
             V.t_val = tvd;
         }
-        if ((rc = dalloc(ctx, &V.x, V.n))) return rc;
+        if (l > 0 && (rc = dalloc(ctx, &V.x, V.n))) return rc;
         if ((rc = dalloc(ctx, &V.rpre, V.n))) return rc;
     }
+    if ((rc = dalloc(ctx, &P.amg_x0, n0))) return rc;
     float* a;
     if ((rc = upload(ctx, &a, ainv.data(), ainv.size()))) return rc;
     P.ainv = a;

@@ -91,8 +91,8 @@ struct Level {
     const int* t_col;        // (the support of a smoothed aggregate), one warp
     const float* t_val;      // takes one row
     const float* dinv;       // 1 / diag(A_l)
-    float* b;                // right-hand side (level 0: the FP32 residual)
-    float* x;                // omega D^-1 b
+    float* b;                // right-hand side (level 0: unused, the FP32 residual)
+    float* x;                // omega D^-1 b (level 0: unused, amg_x0)
     float* rpre;             // b - A x
     float* y;                // output (level 0: the preconditioned residual)
 };
@@ -151,6 +151,7 @@ struct Problem {
     int nlev;                // smoothed levels (0: no hierarchy)
     int nco;                 // rows of the coarsest level (solved densely)
     Level lev[MM_MAXLEV];
+    float* amg_x0;           // [nphi] omega D^-1 r of the FP32 residual r
     const float* ainv;       // [nco][nco] inverse of the coarsest operator
     float* bco;              // [nco] coarsest right-hand side
     float* yco;              // [nco] coarsest solution

@@ -431,51 +431,127 @@ __device__ bool ph_pzero(Ctx& C) {
 // operator, vectors and products; FP64 reductions); then phi += delta and
 // r -= K delta in FP64 (iterative refinement of the FP64 residual).
 
-// One warp's dot product of a CSR row with x (lanes stride the row, four
-// independent loads in flight per lane; fixed summation order).
-__device__ __forceinline__ float warp_csr_dot(const long long* __restrict__ ptr, const int* __restrict__ col,
-                                              const float* __restrict__ val, const float* x, int row,
-                                              int lane) {
-    const long long e = ptr[row + 1];
-    long long k = ptr[row] + lane;
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-    for (; k + 96 < e; k += 128) {
-        const int c0 = __ldg(col + k), c1 = __ldg(col + k + 32), c2 = __ldg(col + k + 64),
-                  c3 = __ldg(col + k + 96);
-        const float v0 = __ldg(val + k), v1 = __ldg(val + k + 32), v2 = __ldg(val + k + 64),
-                    v3 = __ldg(val + k + 96);
-        s0 += v0 * x[c0];
-        s1 += v1 * x[c1];
-        s2 += v2 * x[c2];
-        s3 += v3 * x[c3];
+// Compensated FP32 accumulation (Ogita, Rump and Oishi, "Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): the
+// rounding error of every product (by FMA) and of every addition (by the
+// two-sum transformation) is collected in a second FP32 word, so the result
+// is as accurate as if computed in twice the working precision.  The
+// restriction rows of the smoothed aggregates sum a few hundred terms that
+// largely cancel; their rounding would otherwise enter the coarse
+// correction amplified by the coarse inverse.
+struct Dot2 {
+    float p, s;
+};
+
+// (The _rn intrinsics keep the compiler from contracting the transformations
+// into FMAs, which would break their exactness.)
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+    const float x = __fadd_rn(a, b);
+    const float z = __fsub_rn(x, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(x, z)), __fsub_rn(b, z));
+    return x;
+}
+
+__device__ __forceinline__ void dot2_add(Dot2& d, float a, float b) {
+    const float h = __fmul_rn(a, b);
+    const float r = __fmaf_rn(a, b, -h);     // exact: a b = h + r
+    float q;
+    d.p = two_sum(d.p, h, q);
+    d.s = __fadd_rn(d.s, __fadd_rn(q, r));
+}
+
+__device__ __forceinline__ void dot2_merge(Dot2& d, float p, float s) {
+    float q;
+    d.p = two_sum(d.p, p, q);
+    d.s = __fadd_rn(d.s, __fadd_rn(s, q));
+}
+
+__device__ __forceinline__ float dot2_warp(Dot2 d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float p = __shfl_xor_sync(0xffffffffu, d.p, o);
+        const float s = __shfl_xor_sync(0xffffffffu, d.s, o);
+        dot2_merge(d, p, s);
     }
-    for (; k < e; k += 32) s0 += __ldg(val + k) * x[__ldg(col + k)];
-    return warp_sum_t<float>((s0 + s1) + (s2 + s3));
+    return d.p + d.s;
+}
+
+// One warp's dot products of two CSR rows r0, r1 (r1 < 0: none) with x,
+// compensated.  Each lane loads CH entries of both rows (predicated, all
+// issued before any gather) per pass, so a warp keeps two rows' worth of
+// loads in flight.
+template <int CH, class XF>
+__device__ __forceinline__ void warp_csr_dot2(const long long* __restrict__ ptr, const int* __restrict__ col,
+                                              const float* __restrict__ val, XF x, int r0, int r1, int lane,
+                                              float& out0, float& out1) {
+    const long long b0 = ptr[r0], e0 = ptr[r0 + 1];
+    const long long b1 = r1 >= 0 ? ptr[r1] : 0, e1 = r1 >= 0 ? ptr[r1 + 1] : 0;
+    Dot2 s0 = {0.0f, 0.0f}, s1 = {0.0f, 0.0f};
+    const long long span = (e0 - b0 > e1 - b1) ? e0 - b0 : e1 - b1;
+    for (long long o = 0; o < span; o += 32 * CH) {
+        int c0[CH], c1[CH];
+        float v0[CH], v1[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const long long k0 = b0 + o + 32 * u + lane, k1 = b1 + o + 32 * u + lane;
+            const bool ok0 = k0 < e0, ok1 = k1 < e1;
+            c0[u] = ok0 ? __ldg(col + k0) : 0;
+            v0[u] = ok0 ? __ldg(val + k0) : 0.0f;
+            c1[u] = ok1 ? __ldg(col + k1) : 0;
+            v1[u] = ok1 ? __ldg(val + k1) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            dot2_add(s0, v0[u], x(c0[u]));
+            dot2_add(s1, v1[u], x(c1[u]));
+        }
+    }
+    out0 = dot2_warp(s0);
+    out1 = dot2_warp(s1);
 }
 
 // ---- smoothed-aggregation multigrid V-cycle (the FP32 solve's
 // preconditioner when a hierarchy exists and prm.amg is set); operators as
-// in struct Level.  Down phase of level l: rpre = b - A x on its rows (one
-// thread per row) and b_{l+1} = U^T b, x_{l+1} = omega D^-1 b_{l+1} on the
-// rows of level l+1 (one warp per row).
-__device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
-    const Problem& P = *C.P;
-    Team& t = C.t;
-    const Level& V = P.lev[l];
+// in struct Level.  A down phase computes rpre = b - A x on the rows of its
+// level (one thread per row) and b_{l+1} = U^T b, x_{l+1} = omega D^-1
+// b_{l+1} on the rows of the next level (one warp per row, two rows at a
+// time).  The warps take the coarse rows from the end of the grid, so on
+// the small levels, where the fine rows occupy only the first blocks, both
+// parts run side by side.
+
+// Restriction rows of a down phase: b_{l+1} = U^T b with b(j) given by bx.
+template <class XF>
+__device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, const Level& V, int l, XF bx) {
     const bool last = (l + 1 == P.nlev);
     float* bn = last ? P.bco : P.lev[l + 1].b;
     float* xn = last ? nullptr : P.lev[l + 1].x;
     const float* dn = last ? nullptr : P.lev[l + 1].dinv;
-    const float* b = V.b;
-    ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<8, float>(V.sptr, V.col, V.val, V.x, r);
-    const int lane = threadIdx.x & 31, wpb = MM_BLOCK / 32;
-    for (int I = t.rank * wpb + (int)(threadIdx.x >> 5); I < V.nc; I += t.nb * wpb) {
-        const float s = warp_csr_dot(V.t_ptr, V.t_col, V.t_val, b, I, lane);
+    const int lane = threadIdx.x & 31, wpb = MM_BLOCK / 32, nw = t.nb * wpb;
+    const int w = nw - 1 - (t.rank * wpb + (int)(threadIdx.x >> 5));
+    for (int I = w; I < V.nc; I += 2 * nw) {
+        const int J = (I + nw < V.nc) ? I + nw : -1;
+        float s0, s1;
+        warp_csr_dot2<8>(V.t_ptr, V.t_col, V.t_val, bx, I, J, lane, s0, s1);
         if (lane == 0) {
-            bn[I] = s;
-            if (!last) xn[I] = P.amg_omega * dn[I] * s;
+            bn[I] = s0;
+            if (!last) xn[I] = P.amg_omega * dn[I] * s0;
+        } else if (lane == 1 && J >= 0) {
+            bn[J] = s1;
+            if (!last) xn[J] = P.amg_omega * dn[J] * s1;
         }
     }
+}
+
+// Down phase of level l; at level 0, b is the FP32 residual and x = omega
+// D^-1 b has been written with it by the update step.
+__device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const Level& V = P.lev[l];
+    const float* b = (l == 0) ? P.pres32 : V.b;
+    const float* x = (l == 0) ? P.amg_x0 : V.x;
+    ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
+    amg_restrict(P, t, V, l, [=](int j) { return b[j]; });
     return team_sync(t);
 }
 
@@ -488,6 +564,7 @@ __device__ __noinline__ bool ph_amg_dense(Ctx& C) {
     for (int row = t.rank * wpb + (int)(threadIdx.x >> 5); row < n; row += t.nb * wpb) {
         const float* a = P.ainv + (size_t)row * n;
         float s = 0.0f;
+#pragma unroll 8
         for (int j = lane; j < n; j += 32) s += a[j] * P.bco[j];
         s = warp_sum_t<float>(s);
         if (lane == 0) P.yco[row] = s;
@@ -502,10 +579,11 @@ __device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
     Team& t = C.t;
     const Level& V = P.lev[l];
     const float* yc = (l + 1 == P.nlev) ? P.yco : P.lev[l + 1].y;
+    const float* bv = (l == 0) ? P.pres32 : V.b;
     float acc[2] = {0.0f, 0.0f};
     ROWS(r, V.n) {
-        const float s = sell_dot<8, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0);
-        const float b = V.b[r];
+        const float s = sell_dot<16, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0);
+        const float b = bv[r];
         const float y = P.amg_omega * V.dinv[r] * (b + V.rpre[r]) + s;
         V.y[r] = y;
         acc[0] += b * y;
@@ -520,7 +598,8 @@ __device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
 }
 
 // z = V-cycle(r) for r = pres32, whose smoothed iterate amg_x0 = omega
-// D^-1 r has been written (and a barrier passed) by the caller.
+// D^-1 r has been written (and a barrier passed) by the caller.  Sums r.z,
+// |r|^2.
 __device__ bool amg_vcycle(Ctx& C, double& rz, double& rr) {
     const Problem& P = *C.P;
     for (int l = 0; l < P.nlev; ++l)
@@ -538,11 +617,10 @@ __device__ bool ph_p32_init(Ctx& C, double& rz, double& rr) {
     const Problem& P = *C.P;
     Team& t = C.t;
     if (use_amg(P)) {
-        float* x0 = P.lev[0].x;
         ROWS(p, P.nphi) {
             const float r = (float)P.pres[p];
             P.pres32[p] = r;
-            x0[p] = P.amg_omega * P.dinvP32[p] * r;
+            P.amg_x0[p] = P.amg_omega * P.dinvP32[p] * r;
             P.pdelta32[p] = 0.0f;
         }
         if (!team_sync(t)) return false;
@@ -591,12 +669,32 @@ __device__ bool ph_p32_update(Ctx& C, float a, double& rz, double& rr) {
     const Problem& P = *C.P;
     Team& t = C.t;
     if (use_amg(P)) {
-        float* x0 = P.lev[0].x;
-        ROWS(p, P.nphi) {
-            P.pdelta32[p] += a * P.pdir32[p];
-            const float r = P.pres32[p] - a * P.pq32[p];
-            P.pres32[p] = r;
-            x0[p] = P.amg_omega * P.dinvP32[p] * r;
+        // two rows per pass, all loads first (a streaming pass; no sums here,
+        // r.z and |r|^2 come with z from the V-cycle)
+        const int S = t.nb * MM_BLOCK;
+        float* __restrict__ res = P.pres32;
+        float* __restrict__ del = P.pdelta32;
+        float* __restrict__ x0 = P.amg_x0;
+        const float* __restrict__ dir = P.pdir32;
+        const float* __restrict__ qv = P.pq32;
+        const float* __restrict__ dv = P.dinvP32;
+        const float om = P.amg_omega;
+        for (int p = t.rank * MM_BLOCK + (int)threadIdx.x; p < P.nphi; p += 2 * S) {
+            const int p2 = p + S;
+            const bool two = p2 < P.nphi;
+            const float d1 = dir[p], q1 = qv[p], r1 = res[p], e1 = del[p], w1 = dv[p];
+            const float d2 = two ? dir[p2] : 0.0f, q2 = two ? qv[p2] : 0.0f, r2 = two ? res[p2] : 0.0f,
+                        e2 = two ? del[p2] : 0.0f, w2 = two ? dv[p2] : 0.0f;
+            const float n1 = r1 - a * q1;
+            del[p] = e1 + a * d1;
+            res[p] = n1;
+            x0[p] = om * w1 * n1;
+            if (two) {
+                const float n2 = r2 - a * q2;
+                del[p2] = e2 + a * d2;
+                res[p2] = n2;
+                x0[p2] = om * w2 * n2;
+            }
         }
         if (!team_sync(t)) return false;
         return amg_vcycle(C, rz, rr);
