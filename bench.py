@@ -61,14 +61,46 @@ def workload_desc(name, wl, sizes=None):
 
 
 # ------------------------------------------------------------ algorithmic bytes
-def alg_bytes(st, sz):
+def form_params(form):
+    """Parameters of the three forms of a field step: 0 plain FP64
+    (Jacobi-preconditioned potential solve), 1 precision form with Jacobi,
+    2 precision form with the multigrid preconditioner (the headline)."""
+    from paper_1801_03690_gb300 import Params
+    if form == 0:
+        return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=0)
+    if form == 1:
+        return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1)
+    return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1, amg=1, inner_tol=1e-3)
+
+
+def vcycle_bytes(amg):
+    """Bytes of one multigrid V-cycle (levels l < L smoothed, L dense):
+      down_l  8 nnz_A_l + 12 n_l + 8 nnz_U_l + 12 n_{l+1} (4 n_L at the last)
+              (A and U^T val+col; x, b read, rpre written; b, x of l+1 written)
+      dense   4 n_L^2 + 8 n_L
+      up_l    8 nnz_U_l + 4 n_{l+1} + 16 n_l (U; y_{l+1}; b, rpre, diag^-1 -> y)"""
+    L = len(amg) - 1
+    tot = 4 * amg[L]["nnz_a"] + 8 * amg[L]["rows"]
+    for l in range(L):
+        n, nc = amg[l]["rows"], amg[l + 1]["rows"]
+        tot += 8 * amg[l]["nnz_a"] + 12 * n + 8 * amg[l]["nnz_u"] + (4 if l + 1 == L else 12) * nc
+        tot += 8 * amg[l]["nnz_u"] + 4 * nc + 16 * n
+    return tot
+
+
+def alg_bytes(st, sz, amg=None):
     """Bytes one minimisation launch must move at ideal reuse (every array
     element read or written once per phase, neighbour gathers served from
     cache), from the launch's own counters:
       potential step (mi)   FP64: 12 nnz_phi + 96 n_phi (SELL val+col; z gather,
                             d, q read+write; phi, d, r, q, diag^-1 -> phi, r, z)
                             precision form: FP32 steps 8 nnz_phi + 52 n_phi,
-                            FP64 refinements (mr) 12 nnz_phi + 60 n_phi
+                            FP64 refinements (mr) 12 nnz_phi + 60 n_phi;
+                            with the multigrid preconditioner (amg = the
+                            hierarchy's levels) an FP32 step is the
+                            direction pass 8 nnz_phi + 20 n_phi, the update
+                            pass 32 n_phi and a V-cycle (vcycle_bytes), a
+                            refinement adds a V-cycle
       evaluation (evals)    12 nnz_phi + 64 nnz_mag + 48 n_phi + 208 n_mag
                             (potential set-up incl. D m; energy/gradient pass)
       trial point (evals-1) 112 n_mag
@@ -85,6 +117,10 @@ def alg_bytes(st, sz):
     per_inner = 12 * nzm + 352 * nm
     per_iter = 272 * nm
     mr = st.get("mr", 0)
+    if amg:
+        vc = vcycle_bytes(amg)
+        per_pcg32 = 8 * nzp + 20 * nphi + 32 * nphi + vc
+        per_refine += vc
     steps = (st["mi"] - mr) * per_pcg32 + mr * per_refine if mr else st["mi"] * per_pcg
     return (steps + st["evals"] * per_eval + max(st["evals"] - 1, 0) * per_trial
             + st["li"] * per_inner + (st["nli"] + 1) * per_iter)
@@ -241,7 +277,7 @@ def main():
                          "batch: the batched platelet workload; scaling: field steps of the hard "
                          "cube at several resolutions")
     ap.add_argument("--n-platelets", type=int, default=64)
-    ap.add_argument("--forms", default="plain_fp64,precision,precision_learned")
+    ap.add_argument("--forms", default="plain_fp64,precision,precision_multigrid,precision_learned")
     ap.add_argument("--theta-max", type=float, default=0.1,
                     help="curve mode: line-search cap on the largest nodal step (the paper's reading: 0.1)")
     ap.add_argument("--max-change", type=float, default=0.02,
@@ -296,9 +332,11 @@ def main():
     ranks = Ranks(world, torch.device("cuda", local_rank))
     barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
-    def run_form(precision):
+    amg = mag.amg_info()
+
+    def run_form(prm):
         """W untimed field steps from m0, then K timed field steps."""
-        prm = Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=precision)
+        lv = amg if prm.amg else None
         mag.set_magnetization(wl.m0)
         for k in range(W):
             mag.set_field(fields[k])
@@ -317,7 +355,7 @@ def main():
             st = mag.get_stats()
             ms = mag.last_kernel_ms()
             kern_ms += ms
-            nbytes += alg_bytes(st, sz)
+            nbytes += alg_bytes(st, sz, lv)
             nli += st["nli"]
             per_step.append({"field_T": float(fields[k][2]), "status": st["status"], "nli": st["nli"],
                              "evals": st["evals"], "mi": st["mi"], "mr": st["mr"], "li": st["li"],
@@ -332,8 +370,9 @@ def main():
                 "kern_ms": kern_ms, "bytes": nbytes, "per_step": per_step, "clocks": ck,
                 "m": mag.get_magnetization(), "F": per_step[-1]["F_J"]}
 
-    fp64 = run_form(0)
-    x1 = run_form(1)
+    fp64 = run_form(form_params(0))
+    jac = run_form(form_params(1))
+    x1 = run_form(form_params(2))
 
     # ---- end to end through the public API with host buffers (precision form)
     e2e = None
@@ -376,6 +415,7 @@ def main():
     achieved = x1["bytes"] / (x1["kern_ms"] / 1000.0) / 1e9
     ratio = traffic_ratio()
     ach64 = fp64["bytes"] / (fp64["kern_ms"] / 1000.0) / 1e9
+    achj = jac["bytes"] / (jac["kern_ms"] / 1000.0) / 1e9
     dm = float(np.abs(x1["m"] - fp64["m"]).max())
     line = {
         "metric": METRIC, "value": x1["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -390,20 +430,29 @@ def main():
         "plain_fp64": {"value": fp64["value"], "unit": UNIT, "ms_per_step": fp64["t_ms"] / K,
                        "dtype": "f64", "roofline_frac": ach64 / hbm, "achieved_gbs": ach64,
                        "per_step": fp64["per_step"]},
+        "precision_jacobi": {"value": jac["value"], "unit": UNIT, "ms_per_step": jac["t_ms"] / K,
+                             "dtype": "fp32+fp64", "roofline_frac": achj / hbm, "achieved_gbs": achj,
+                             "per_step": jac["per_step"]},
+        "multigrid": {"levels": amg, "inner_tol": x1["prm"].inner_tol},
         "demag_curve": {"fields_timed": K, "wall_s_precision_form": x1["t_ms"] / 1000.0,
                         "wall_s_plain_fp64": fp64["t_ms"] / 1000.0,
+                        "wall_s_precision_jacobi": jac["t_ms"] / 1000.0,
                         "speedup_vs_plain_fp64": fp64["t_ms"] / x1["t_ms"],
+                        "speedup_vs_precision_jacobi": jac["t_ms"] / x1["t_ms"],
                         "final_energy_rel_diff": abs(x1["F"] - fp64["F"]) / abs(fp64["F"]),
                         "final_max_abs_dm": dm, "per_step": x1["per_step"]},
         "gpu_launches": 2 * K,
     }
-    line["config"]["precision"] = "precision form: FP32 potential solve + FP64 refinement (plain FP64 in plain_fp64)"
+    line["config"]["precision"] = ("precision form: FP32 potential solve preconditioned by the multigrid V-cycle "
+                                   "+ FP64 refinement (Jacobi-preconditioned in precision_jacobi, plain FP64 "
+                                   "in plain_fp64)")
     if e2e:
         line["e2e"] = e2e
     if x1["clocks"]:
         line["clocks"] = x1["clocks"]
-        if fp64["clocks"]:
-            line["clocks"]["reasons"] = sorted(set(x1["clocks"]["reasons"]) | set(fp64["clocks"]["reasons"]))
+        for o in (fp64, jac):
+            if o["clocks"]:
+                line["clocks"]["reasons"] = sorted(set(line["clocks"]["reasons"]) | set(o["clocks"]["reasons"]))
     if world == 1 and not args.no_cpu_baseline:
         nli_c, dt_c, desc = oracle_sample(wl, max_iter=1)
         line["cpu_baseline"] = {"value": nli_c / dt_c, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -414,8 +463,9 @@ def main():
 
 
 def curve_mode(args, rank, local_rank):
-    """Full demagnetisation curves of one workload in three forms: plain
-    FP64, the precision form, and the precision form with the learned warm
+    """Full demagnetisation curves of one workload in four forms: plain FP64,
+    the precision form with the Jacobi and with the multigrid potential
+    preconditioner, and the multigrid precision form with the learned warm
     start (network trained on the curve of a coarser mesh of the same
     recipe).  Reports wall time, NCG iterations and coercive field."""
     import torch
@@ -453,6 +503,7 @@ def curve_mode(args, rank, local_rank):
 
     run("plain_fp64", Params(precision=0, theta_max=args.theta_max))
     run("precision", Params(precision=1, theta_max=args.theta_max))
+    run("precision_multigrid", Params(precision=1, amg=1, inner_tol=1e-3, theta_max=args.theta_max))
     # learned warm start: train on the curve of the same recipe at half the resolution
     if "precision_learned" not in forms:
         if rank == 0:
@@ -466,14 +517,16 @@ def curve_mode(args, rank, local_rank):
         coarse = synth.hard_cube(n_mag=12, seed=12, n_fields=len(fields))
     tm = Magnet(device=local_rank)
     tm.upload_workload(coarse)
-    X, T, _ = warmstart.collect(tm, coarse.m0, coarse.fields, tm.sizes()["n_mag"], Params(precision=1))
+    X, T, _ = warmstart.collect(tm, coarse.m0, coarse.fields, tm.sizes()["n_mag"],
+                                Params(precision=1, amg=1, inner_tol=1e-3))
     tm.close()
     net = MLP(device=local_rank, seed=11)
     s_m, s_p, losses = warmstart.train(net, X, T, steps=1500, batch=16384, lr=2e-3, log_every=500)
     train_s = time.perf_counter() - t0
-    run("precision_learned", Params(precision=1, theta_max=args.theta_max), net=net, scales=(s_m, s_p))
+    run("precision_learned", Params(precision=1, amg=1, inner_tol=1e-3, theta_max=args.theta_max), net=net,
+        scales=(s_m, s_p))
     ref = out.get("plain_fp64") or out.get("precision")
-    for k in ("precision", "precision_learned"):
+    for k in ("precision", "precision_multigrid", "precision_learned"):
         if k not in out or out[k] is ref:
             continue
         o = out[k]
@@ -494,17 +547,19 @@ def curve_mode(args, rank, local_rank):
 def scaling_mode(args, rank, local_rank):
     """Size sweep at fixed physics (the 80 nm hard cube at several
     resolutions, air box 2x): NCG iterations and potential CG steps per field
-    step, throughput, achieved bandwidth (precision form, field steps 3-7)."""
+    step, throughput, achieved bandwidth (field steps 3-7), for the precision
+    form with the Jacobi and with the multigrid potential preconditioner."""
     import torch
     import synth
-    from paper_1801_03690_gb300 import Magnet, Params
-    prm = Params(precision=1)
+    from paper_1801_03690_gb300 import Magnet
     rows = []
-    for n in (16, 24, 32, 40, 48, 56, 64):
+    for n, form in [(n, f) for n in (16, 24, 32, 40, 48, 56, 64) for f in (1, 2)]:
+        prm = form_params(form)
         wl = synth.hard_cube(n_mag=n)
         mag = Magnet(device=local_rank)
         mag.upload_workload(wl)
         sz = mag.sizes()
+        lv = mag.amg_info() if prm.amg else None
         mag.set_magnetization(wl.m0)
         for k in range(3):
             mag.set_field(wl.fields[k])
@@ -518,12 +573,14 @@ def scaling_mode(args, rank, local_rank):
             mag.minimize_async(prm)
             st = mag.get_stats()
             kms += mag.last_kernel_ms()
-            nbytes += alg_bytes(st, sz)
+            nbytes += alg_bytes(st, sz, lv)
             nli += st["nli"]
             mi += st["mi"]
             ev += st["evals"]
         dt = time.perf_counter() - t0
-        rows.append({"n_mag_voxels": n, "n_mag": sz["n_mag"], "n_phi": sz["n_phi"],
+        rows.append({"form": "multigrid" if prm.amg else "jacobi",
+                     "levels": [lvl["rows"] for lvl in lv] if lv else None,
+                     "n_mag_voxels": n, "n_mag": sz["n_mag"], "n_phi": sz["n_phi"],
                      "nli_per_step": nli / 5, "cg_steps_per_eval": mi / ev, "NCG_it_per_s": nli / dt,
                      "ms_per_step": 1000 * dt / 5, "achieved_GBs": nbytes / (kms / 1000) / 1e9})
         mag.close()

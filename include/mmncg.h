@@ -141,10 +141,14 @@ int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi,
 
 /* Multigrid hierarchy of the potential solve built by mm_upload_mesh
  * (Sec. 3.1 preconditions that solve with algebraic multigrid): *n_levels
- * smoothed levels (0: none, mm_params.amg then falls back to Jacobi) and
- * rows[0..n_levels] the rows of every level, the last the coarsest (solved
- * with a dense inverse).  rows may be NULL; at most max_rows are written. */
-int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int32_t max_rows);
+ * smoothed levels L (0: none; mm_params.amg then runs Jacobi) and, for
+ * l = 0..L, rows[l] the rows of level l (level L is the coarsest, solved
+ * with a dense inverse), nnz_a[l] the nonzeros of its operator (level 0:
+ * K_phi; level L: rows[L]^2 entries of the dense inverse) and, for l < L,
+ * nnz_u[l] the nonzeros of its smoothed prolongation U_l.  Any output may
+ * be NULL; at most max_entries entries are written per array. */
+int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nnz_a,
+                int64_t* nnz_u, int32_t max_entries);
 
 /* Magnetisation per node ([n_nodes][3]); normalised on entry (N m, Eq. opt2). */
 int mm_set_magnetization(mm_ctx* ctx, const double* m);

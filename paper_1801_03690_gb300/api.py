@@ -122,10 +122,18 @@ class Magnet:
     def amg_levels(self):
         """Rows of every level of the potential solve's multigrid hierarchy,
         finest first, coarsest (dense) last; [] when there is none."""
+        return [lv["rows"] for lv in self.amg_info()]
+
+    def amg_info(self):
+        """Per level of the multigrid hierarchy: rows, nonzeros of the
+        operator (nnz_a; the coarsest: entries of its dense inverse) and of
+        the smoothed prolongation (nnz_u; None at the coarsest)."""
         n = C.c_int32()
-        rows = (C.c_int64 * (64))()
-        self._check(self._lib.mm_amg_info(self._h, C.byref(n), rows, 64))
-        return [int(rows[l]) for l in range(n.value + 1)] if n.value > 0 else []
+        rows, na, nu = [(C.c_int64 * 64)() for _ in range(3)]
+        self._check(self._lib.mm_amg_info(self._h, C.byref(n), rows, na, nu, 64))
+        L = n.value
+        return [{"rows": int(rows[l]), "nnz_a": int(na[l]), "nnz_u": int(nu[l]) if l < L else None}
+                for l in range(L + 1)] if L > 0 else []
 
     # ----------------------------------------------------------------- state
     def set_magnetization(self, m):

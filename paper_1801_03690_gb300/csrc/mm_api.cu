@@ -107,6 +107,7 @@ struct mm_ctx {
     int nm = 0, nphi = 0;
     long long nnzm = 0, nnzp = 0;         // padded SELL entries
     long long nnzm_true = 0, nnzp_true = 0;
+    std::vector<long long> amg_nnz_a, amg_nnz_u;   // per multigrid level (host copy)
     double Mref = 0.0;
     double field_T[3] = {0, 0, 0};
     std::vector<void*> allocs;            // device buffers of the mesh
@@ -480,6 +481,8 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
     P.nlev = 0;
     P.nco = 0;
     P.amg_omega = (float)kAmgOmega;
+    ctx->amg_nnz_a.clear();
+    ctx->amg_nnz_u.clear();
     const int n0 = P.nphi;
     if (n0 <= kCoarseDense) return MM_OK;
     HostCsr A;
@@ -500,6 +503,7 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
             A.ptr[r + 1] = (long long)A.col.size();
         }
     }
+    const long long nnz0 = (long long)A.col.size();
     struct Host {
         HostCsr U, Ut;
         std::vector<float> dinv;
@@ -589,6 +593,10 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
     if ((rc = dalloc(ctx, &P.bco, A.n))) return rc;
     if ((rc = dalloc(ctx, &P.yco, A.n))) return rc;
     P.nlev = L;
+    ctx->amg_nnz_a.push_back(nnz0);
+    for (const HostCsr& o : ops) ctx->amg_nnz_a.push_back((long long)o.col.size());
+    ctx->amg_nnz_a.back() = (long long)A.n * A.n;               // the dense inverse
+    for (const Host& h : host) ctx->amg_nnz_u.push_back((long long)h.U.col.size());
     return MM_OK;
 }
 
@@ -1197,12 +1205,17 @@ int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi, int64_t* nnz_mag
     return MM_OK;
 }
 
-int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int32_t max_rows) {
+int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nnz_a, int64_t* nnz_u,
+                int32_t max_entries) {
     if (!ctx || !ctx->has_mesh) return MM_ERR_STATE;
     const mm::Problem& P = ctx->P;
     if (n_levels) *n_levels = P.nlev;
-    if (rows)
-        for (int l = 0; l <= P.nlev && l < max_rows; ++l) rows[l] = (l < P.nlev) ? P.lev[l].n : P.nco;
+    if (P.nlev == 0) return MM_OK;
+    for (int l = 0; l <= P.nlev && l < max_entries; ++l) {
+        if (rows) rows[l] = (l < P.nlev) ? P.lev[l].n : P.nco;
+        if (nnz_a) nnz_a[l] = ctx->amg_nnz_a[l];
+        if (nnz_u && l < P.nlev) nnz_u[l] = ctx->amg_nnz_u[l];
+    }
     return MM_OK;
 }
 
