@@ -69,7 +69,7 @@ typedef struct {
 
 typedef struct {
     int device;           /* CUDA device ordinal                                 */
-    int blocks_per_sm;    /* solver kernel built for 2, 3 or 4 blocks/SM (0 = 3) */
+    int blocks_per_sm;    /* solver kernel built for 2, 3 or 4 blocks/SM (0 = 2) */
     void* stream;         /* cudaStream_t to run on; NULL = a private stream     */
 } mm_options;
 

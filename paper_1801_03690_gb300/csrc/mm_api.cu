@@ -803,9 +803,10 @@ int mm_create(mm_ctx** out, const mm_options* opt) {
     if (!coop) return bail(MM_ERR_CUDA);
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     // blocks_per_sm selects the kernel instantiation (register budget) and
-    // the grid: 2, 3 or 4 blocks per SM (0 or anything else = 3, the fastest
-    // measured on GB300).
-    const int variant = (ctx->blocks_per_sm_req >= 2 && ctx->blocks_per_sm_req <= 4) ? ctx->blocks_per_sm_req : 3;
+    // the grid: 2, 3 or 4 blocks per SM (0 or anything else = 2: measured on
+    // GB300 with the bench mesh, 2 is fastest for the Jacobi forms and ties
+    // with 3 for the multigrid form; its 128-register budget spills least).
+    const int variant = (ctx->blocks_per_sm_req >= 2 && ctx->blocks_per_sm_req <= 4) ? ctx->blocks_per_sm_req : 2;
     ctx->kernel = mm::solver_kernel(variant);
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ctx->kernel, MM_BLOCK, 0) != cudaSuccess || bps < 1)
