@@ -16,7 +16,7 @@
 namespace {
 
 constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
-constexpr int kBarWords = 64;      // per team: [0] count, [32] generation
+constexpr int kBarWords = 64;      // per team: [0..1] the 64-bit arrival counter
 constexpr int kErrWords = 32;      // per team error flag, one 128-byte line
 
 __global__ void k_batch_fields(int n, const double* fields, const int* step, mm::DevState* const* states) {

@@ -158,7 +158,7 @@ struct Problem {
     float amg_omega;         // Jacobi damping of the smoother
     // team machinery
     double* partials;        // [2][MM_MAXRED][nblocks]
-    unsigned* bar;           // [0] = arrival count, [32] = generation
+    unsigned* bar;           // [0..1] = 64-bit arrival counter of the team barrier
     int* err;                // device error flag
     DevState* state;
     Params prm;
