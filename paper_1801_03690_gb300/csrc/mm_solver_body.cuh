@@ -279,10 +279,10 @@ __device__ __forceinline__ void sell_dot3(const long long* __restrict__ sptr, co
 
 // Two SELL-32 rows r0 and r1 = r0 + team stride (two: r1 exists) per thread,
 // CH entries of both rows loaded before any gather: twice the loads in
-// flight of the one-row form at the same register cost as CH = 16 (measured
-// on GB300 inside the solver kernel: 20.7 vs 24.6 us for the FP32 K_phi
-// product of the 857k-row bench matrix).  Lanes past a row's width read
-// x[pad].
+// flight of the one-row form at the register cost of CH = 16.  Used by the
+// FP32 direction step (33.8 vs 34.9 us on the bench mesh at 2 blocks/SM);
+// the multigrid products measured no better than one row with CH = 16.
+// Lanes past a row's width read x[pad].
 template <int CH, typename VT>
 __device__ __forceinline__ void sell_dot_2rows(const long long* __restrict__ sptr, const int* __restrict__ col,
                                                const VT* __restrict__ val, const VT* x, int r0, int r1,
@@ -590,16 +590,7 @@ __device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
     const Level& V = P.lev[l];
     const float* b = (l == 0) ? P.pres32 : V.b;
     const float* x = (l == 0) ? P.amg_x0 : V.x;
-    if (V.n > t.nb * MM_BLOCK) {
-        ROWS2(r, r2, two, V.n) {
-            float s0, s1;
-            sell_dot_2rows<8>(V.sptr, V.col, V.val, x, r, r2, two, r, s0, s1);
-            V.rpre[r] = b[r] - s0;
-            if (two) V.rpre[r2] = b[r2] - s1;
-        }
-    } else {                                   // a small level: one row per thread
-        ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
-    }
+    ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
     amg_restrict(P, t, V, l, [=](int j) { return b[j]; });
     return team_sync(t);
 }
@@ -637,16 +628,7 @@ __device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
         acc[0] += b * y;
         acc[1] += b * b;
     };
-    if (V.n > t.nb * MM_BLOCK) {
-        ROWS2(r, r2, two, V.n) {
-            float s0, s1;
-            sell_dot_2rows<8>(V.u_sptr, V.u_col, V.u_val, yc, r, r2, two, 0, s0, s1);
-            row(r, s0);
-            if (two) row(r2, s1);
-        }
-    } else {                                   // a small level: one row per thread
-        ROWS(r, V.n) row(r, sell_dot<16, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0));
-    }
+    ROWS(r, V.n) row(r, sell_dot<16, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0));
     if (l > 0) return team_sync(t);
     double out[2];
     if (!team_sum_f32<2>(t, acc, out)) return false;
