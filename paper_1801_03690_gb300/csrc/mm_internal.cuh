@@ -81,6 +81,7 @@ struct DevState {
 struct Level {
     int n;                   // rows of this level
     int nc;                  // rows of the next coarser level
+    float omega;             // Jacobi damping of this level's smoother
     const long long* sptr;   // A_l (level 0: the FP32 copy of K_phi)
     const int* col;
     const float* val;
@@ -155,7 +156,7 @@ struct Problem {
     const float* ainv;       // [nco][nco] inverse of the coarsest operator
     float* bco;              // [nco] coarsest right-hand side
     float* yco;              // [nco] coarsest solution
-    float amg_omega;         // Jacobi damping of the smoother
+    float amg_omega;         // Jacobi damping of the level-0 smoother
     // team machinery
     double* partials;        // [2][MM_MAXRED][nblocks]
     unsigned* bar;           // [0..1] = 64-bit arrival counter of the team barrier

@@ -566,6 +566,7 @@ __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, co
     float* bn = last ? P.bco : P.lev[l + 1].b;
     float* xn = last ? nullptr : P.lev[l + 1].x;
     const float* dn = last ? nullptr : P.lev[l + 1].dinv;
+    const float on = last ? 0.0f : P.lev[l + 1].omega;
     const int lane = threadIdx.x & 31, wpb = MM_BLOCK / 32, nw = t.nb * wpb;
     const int w = nw - 1 - (t.rank * wpb + (int)(threadIdx.x >> 5));
     for (int I = w; I < V.nc; I += 2 * nw) {
@@ -574,10 +575,10 @@ __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, co
         warp_csr_dot2<8>(V.t_ptr, V.t_col, V.t_val, bx, I, J, lane, s0, s1);
         if (lane == 0) {
             bn[I] = s0;
-            if (!last) xn[I] = P.amg_omega * dn[I] * s0;
+            if (!last) xn[I] = on * dn[I] * s0;
         } else if (lane == 1 && J >= 0) {
             bn[J] = s1;
-            if (!last) xn[J] = P.amg_omega * dn[J] * s1;
+            if (!last) xn[J] = on * dn[J] * s1;
         }
     }
 }
@@ -623,7 +624,7 @@ __device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
     float acc[2] = {0.0f, 0.0f};
     auto row = [&](int r, float s) {
         const float b = bv[r];
-        const float y = P.amg_omega * V.dinv[r] * (b + V.rpre[r]) + s;
+        const float y = V.omega * V.dinv[r] * (b + V.rpre[r]) + s;
         V.y[r] = y;
         acc[0] += b * y;
         acc[1] += b * b;
