@@ -593,13 +593,13 @@ def batch_mode(args, rank, local_rank):
     """The batched sensor workload: n permalloy platelets of 5k-80k magnetic
     nodes, minimised at one field in one persistent launch (after the
     autotuner picked the kernel instantiation and team split), against the
-    same problems minimised one after the other."""
+    same problems minimised one after the other, in the precision form with
+    the Jacobi and with the multigrid potential preconditioner."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
     import synth
-    from paper_1801_03690_gb300 import Magnet, Params, Batch
+    from paper_1801_03690_gb300 import Magnet, Batch
     wls = synth.platelet_batch(args.n_platelets)
-    prm = Params(precision=1)
 
     def make(wl):
         m = Magnet(device=local_rank)
@@ -615,50 +615,55 @@ def batch_mode(args, rank, local_rank):
             m.set_magnetization(wl.m0)
             m.set_field(wl.fields[k])
 
-    res = {}
-    reset(0)
-    batch = Batch(mags)
-    bps, gamma, ms = batch.autotune(prm)
-    res["autotune"] = {"blocks_per_sm": bps, "gamma": gamma, "trial_ms": ms}
-    for k in (0, 1, 2):                               # warm-up field steps
-        reset(k) if k == 0 else [m.set_field(wl.fields[k]) for m, wl in zip(mags, wls)]
-        batch.minimize(prm)
+    def run(prm):
+        res = {}
+        reset(0)
+        batch = Batch(mags)
+        bps, gamma, ms = batch.autotune(prm)
+        res["autotune"] = {"blocks_per_sm": bps, "gamma": gamma, "trial_ms": ms}
+        for k in (0, 1, 2):                               # warm-up field steps
+            reset(k) if k == 0 else [m.set_field(wl.fields[k]) for m, wl in zip(mags, wls)]
+            batch.minimize(prm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nli = 0
+        for k in range(3, 3 + K):
+            for m, wl in zip(mags, wls):
+                m.set_field(wl.fields[k])
+            sts = batch.minimize(prm)
+            nli += sum(s["nli"] for s in sts)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        res["batched"] = {"nli": nli, "seconds": tb, "NCG_it_per_s": nli / tb}
+        batch.close()
+        # the same field steps one problem after the other
+        reset(0)
+        for k in (0, 1, 2):
+            for m, wl in zip(mags, wls):
+                m.set_field(wl.fields[k])
+                m.minimize(prm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nli_s = 0
+        for k in range(3, 3 + K):
+            for m, wl in zip(mags, wls):
+                m.set_field(wl.fields[k])
+                nli_s += m.minimize(prm)["nli"]
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        res["sequential"] = {"nli": nli_s, "seconds": ts, "NCG_it_per_s": nli_s / ts}
+        res["speedup"] = ts / tb
+        return res
+
     K = 5
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    nli = 0
-    for k in range(3, 3 + K):
-        for m, wl in zip(mags, wls):
-            m.set_field(wl.fields[k])
-        sts = batch.minimize(prm)
-        nli += sum(s["nli"] for s in sts)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
-    res["batched"] = {"nli": nli, "seconds": tb, "NCG_it_per_s": nli / tb}
-    # the same field steps one problem after the other
-    reset(0)
-    for k in (0, 1, 2):
-        for m, wl in zip(mags, wls):
-            m.set_field(wl.fields[k])
-            m.minimize(prm)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    nli_s = 0
-    for k in range(3, 3 + K):
-        for m, wl in zip(mags, wls):
-            m.set_field(wl.fields[k])
-            nli_s += m.minimize(prm)["nli"]
-    torch.cuda.synchronize()
-    ts = time.perf_counter() - t0
-    res["sequential"] = {"nli": nli_s, "seconds": ts, "NCG_it_per_s": nli_s / ts}
-    res["speedup"] = ts / tb
+    res = {"precision_jacobi": run(form_params(1)), "precision_multigrid": run(form_params(2)),
+           "with_hierarchy": int(sum(1 for m in mags if m.amg_levels()))}
     if rank == 0:
         print(json.dumps({"mode": "batch", "n": len(wls),
                           "n_mag_total": int(sum(s["n_mag"] for s in sizes)),
                           "n_phi_total": int(sum(s["n_phi"] for s in sizes)),
                           "n_mag_range": [int(min(s["n_mag"] for s in sizes)), int(max(s["n_mag"] for s in sizes))],
                           "field_steps_timed": K, **res}))
-    batch.close()
     for m in mags:
         m.close()
     return 0
