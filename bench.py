@@ -47,6 +47,8 @@ def workload(name):
         return synth.hard_cube(n_mag=44)
     if name == "small":
         return synth.hard_cube(n_mag=12)
+    if name == "polycrystal":
+        return synth.polycrystal_cube()
     raise ValueError(name)
 
 
@@ -268,7 +270,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "medium", "soft_cube", "small"])
+    ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "medium", "soft_cube", "small", "polycrystal"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling"],

@@ -91,3 +91,29 @@ def test_first_field_step_reaches_a_minimum(full):
     # t3 at the returned state (internal units)
     assert np.abs(g).max() < 1e-10 ** (1 / 3) * (1 + abs(st["F_internal"]))
     assert st["evals"] == 2 * st["nli"] + 1 + st["ls_extra"]
+
+
+def test_multigrid_form_first_field_step_matches_jacobi_form(full):
+    """The bench's headline form (precision form, multigrid-preconditioned
+    potential solve) at full size, in the launch configuration bench.py
+    times: same minimum as the Jacobi-preconditioned precision form (energy
+    1e-8 relative, max nodal |dm| 1e-5), |m| = 1, t3 at the returned state,
+    and far fewer potential steps."""
+    from paper_1801_03690_gb300 import Params
+    wl, mag = full
+    assert len(mag.amg_levels()) >= 3
+    out = []
+    for prm in (Params(precision=1), Params(precision=1, amg=1, inner_tol=1e-3)):
+        mag.set_magnetization(wl.m0)
+        mag.set_field(wl.fields[1])
+        st = mag.minimize(prm)
+        assert st["status"] == "ok"
+        out.append((st, mag.get_magnetization()))
+    (sj, mj), (sm, mm_) = out
+    assert sm["F"] == pytest.approx(sj["F"], rel=1e-8)
+    assert np.abs(mm_ - mj).max() < 1e-5
+    mag_nodes = np.linalg.norm(mm_, axis=1) > 0
+    np.testing.assert_allclose(np.linalg.norm(mm_[mag_nodes], axis=1), 1.0, atol=1e-13)
+    g = mag.gradient(None, projected=True, params=Params(precision=1, amg=1, inner_tol=1e-3))
+    assert np.abs(g).max() < 1e-10 ** (1 / 3) * (1 + abs(sm["F_internal"]))
+    assert sm["mi"] / sm["evals"] < 0.25 * sj["mi"] / sj["evals"]
