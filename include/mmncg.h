@@ -255,7 +255,7 @@ int mm_batch_plan(int n, const int64_t* work, int total_blocks, double gamma,
 int mm_batch_create(mm_batch** b, int n, mm_ctx* const* ctxs);
 void mm_batch_destroy(mm_batch* b);
 const char* mm_batch_last_error(const mm_batch* b);
-/* Kernel instantiation (3 or 4 blocks per SM) and team-split exponent. */
+/* Kernel instantiation (2, 3 or 4 blocks per SM) and team-split exponent. */
 int mm_batch_config(mm_batch* b, int blocks_per_sm, double gamma);
 /* Minimise every member at its current field from its current m (one
  * launch); stats_out [n] (may be NULL).  Returns the first non-OK status. */

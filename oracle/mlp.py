@@ -1,4 +1,4 @@
-"""CPU reference of the warm-start network (a spec extension; the paper
+"""CPU reference of the warm-start network (an extension of the method; the paper
 has no learned component): a per-node multilayer perceptron
 16 -> 128 -> 128 -> 128 -> 4 with ReLU, trained by mean squared error.
 

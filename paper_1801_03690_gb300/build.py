@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmmncg.so")
-SOURCES = ["mm_kern_s3.cu", "mm_kern_s2.cu", "mm_kern_s4.cu", "mm_kern_b3.cu", "mm_kern_b4.cu",
+SOURCES = ["mm_kern_s3.cu", "mm_kern_s2.cu", "mm_kern_s4.cu", "mm_kern_b2.cu", "mm_kern_b3.cu", "mm_kern_b4.cu",
            "mm_assemble.cu", "mm_api.cu", "mm_noalloc.cu", "mm_batch.cu", "mm_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -719,6 +719,7 @@ namespace mm {
 const void* solver_kernel_2();
 const void* solver_kernel_3();
 const void* solver_kernel_4();
+const void* solver_batch_kernel_2();
 const void* solver_batch_kernel_3();
 const void* solver_batch_kernel_4();
 
@@ -731,7 +732,7 @@ const void* solver_kernel(int min_blocks) {
 }
 
 const void* solver_batch_kernel(int min_blocks) {
-    return min_blocks == 4 ? solver_batch_kernel_4() : solver_batch_kernel_3();
+    return min_blocks == 4 ? solver_batch_kernel_4() : min_blocks == 2 ? solver_batch_kernel_2() : solver_batch_kernel_3();
 }
 
 int ctx_view(mm_ctx* ctx, CtxView* out) {

@@ -306,7 +306,7 @@ const char* mm_batch_last_error(const mm_batch* b) { return b ? b->err.c_str() :
 
 int mm_batch_config(mm_batch* b, int blocks_per_sm, double gamma) {
     if (!b) return MM_ERR_ARG;
-    if (blocks_per_sm != 3 && blocks_per_sm != 4) return bfail(b, MM_ERR_ARG, "blocks_per_sm must be 3 or 4");
+    if (blocks_per_sm < 2 || blocks_per_sm > 4) return bfail(b, MM_ERR_ARG, "blocks_per_sm must be 2, 3 or 4");
     if (!(gamma >= 0.0 && gamma <= 2.0)) return bfail(b, MM_ERR_ARG, "gamma must be in [0, 2]");
     b->variant = blocks_per_sm;
     b->gamma = gamma;
@@ -455,12 +455,12 @@ int mm_batch_autotune(mm_batch* b, const mm_params* p, int* chosen_blocks_per_sm
         }
         return MM_OK;
     };
-    const int variants[2] = {3, 4};
+    const int variants[3] = {2, 3, 4};
     const double gammas[3] = {0.5, 0.75, 1.0};
     double best = 1e300;
     int bv = b->variant;
     double bg = b->gamma;
-    for (int vi = 0; vi < 2; ++vi)
+    for (int vi = 0; vi < 3; ++vi)
         for (int gi = 0; gi < 3; ++gi) {
             b->variant = variants[vi];
             b->gamma = gammas[gi];
