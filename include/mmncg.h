@@ -150,6 +150,20 @@ int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi,
 int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nnz_a,
                 int64_t* nnz_u, int32_t max_entries);
 
+/* Host only (no GPU, no context): build the multigrid hierarchy that
+ * mm_upload_mesh builds for K_phi, for the symmetric positive definite
+ * matrix A given in CSR (row_ptr [n+1], col [nnz], val [nnz], FP64; the
+ * caller keeps ownership), and apply its V-cycle in FP64 to n_vec vectors
+ * r [n_vec][n], writing z [n_vec][n].  This is the cycle the solver kernel
+ * runs in FP32 (same set-up, same algebra), exposed so that the set-up can
+ * be checked without a GPU.  *n_levels and rows as in mm_amg_info; when
+ * there is no hierarchy (n <= 1536, or the coarsening stalls) *n_levels = 0
+ * and z is left untouched.  MM_ERR_ARG for null pointers, n < 1,
+ * decreasing row_ptr or a column outside [0, n). */
+int mm_amg_host_apply(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                      int32_t n_vec, const double* r, double* z, int32_t* n_levels,
+                      int64_t* rows, int32_t max_rows);
+
 /* Magnetisation per node ([n_nodes][3]); normalised on entry (N m, Eq. opt2). */
 int mm_set_magnetization(mm_ctx* ctx, const double* m);
 int mm_get_magnetization(mm_ctx* ctx, double* m_out);

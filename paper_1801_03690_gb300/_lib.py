@@ -56,6 +56,10 @@ EXPORTS = {
     "mm_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int64)] * 4),
     "mm_amg_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                               C.POINTER(C.c_int64), C.c_int32]),
+    "mm_amg_host_apply": (C.c_int, [C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                    C.c_int32]),
     "mm_set_magnetization": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mm_get_magnetization": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mm_set_magnetization_dev": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -244,6 +244,33 @@ def batch_plan(work, total_blocks, gamma=1.0):
     return out
 
 
+def amg_host_apply(indptr, indices, data, R):
+    """The potential solve's multigrid V-cycle applied on the host (FP64, no
+    GPU needed) to the rows of R, for the SPD matrix in CSR form (indptr,
+    indices, data).  Returns (Z, level rows); ([], ...) when the matrix gets
+    no hierarchy, Z is then None."""
+    lib = L.load()
+    ip = np.ascontiguousarray(indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    dv = np.ascontiguousarray(data, dtype=np.float64)
+    n = len(ip) - 1
+    R = np.ascontiguousarray(np.atleast_2d(R), dtype=np.float64)
+    if R.shape[1] != n:
+        raise ValueError("R must have n columns")
+    Z = np.zeros_like(R)
+    nl = C.c_int32()
+    rows = (C.c_int64 * 64)()
+    rc = lib.mm_amg_host_apply(n, ip.ctypes.data_as(C.POINTER(C.c_int64)), ix.ctypes.data_as(C.POINTER(C.c_int32)),
+                               dv.ctypes.data_as(C.POINTER(C.c_double)), R.shape[0],
+                               R.ctypes.data_as(C.POINTER(C.c_double)), Z.ctypes.data_as(C.POINTER(C.c_double)),
+                               C.byref(nl), rows, 64)
+    if rc != 0:
+        raise MMError(rc, "mm_amg_host_apply rejected its arguments")
+    if nl.value == 0:
+        return None, []
+    return Z, [int(rows[l]) for l in range(nl.value + 1)]
+
+
 class Batch:
     """Many independent magnets minimised in one persistent launch."""
 

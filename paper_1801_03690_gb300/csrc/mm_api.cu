@@ -388,10 +388,10 @@ void csr_to_sell(const HostCsr& A, std::vector<long long>& sptr, std::vector<int
     }
 }
 
-// Inverse of a small SPD matrix, FP64, returned row-major in FP32:
+// Inverse of a small SPD matrix, FP64, row-major:
 // A = L L^T (Cholesky), L^-1 row by row, A^-1 = L^-T L^-1.  All inner loops
 // run along rows.  Returns false if A is not numerically positive definite.
-bool dense_inverse(const HostCsr& A, std::vector<float>& inv) {
+bool dense_inverse(const HostCsr& A, std::vector<double>& inv) {
     const int n = A.n;
     std::vector<double> L((size_t)n * n, 0.0), Li((size_t)n * n, 0.0), acc(n);
     for (int i = 0; i < n; ++i)
@@ -432,8 +432,7 @@ bool dense_inverse(const HostCsr& A, std::vector<float>& inv) {
             for (int j = 0; j <= k; ++j) Xi[j] += c * Lk[j];
         }
     }
-    inv.resize((size_t)n * n);
-    for (size_t e = 0; e < inv.size(); ++e) inv[e] = (float)X[e];
+    inv.swap(X);
     return true;
 }
 
@@ -468,19 +467,122 @@ constexpr int kCoarseDense = 1536;      // coarsest level solved by a dense inve
 constexpr double kAmgOmega = 0.9;       // Jacobi damping of the smoother, at most ...
 constexpr double kAmgOmegaRho = 1.95;   // ... 1.95 / rho (rho >= the spectral radius of D^-1 A)
 
-// Smoothed-aggregation multigrid hierarchy of K_phi, built on the host in
-// FP64 from the device SELL layout of level 0 (sptr/col/Kp).  Per level:
-// greedy aggregates, tentative prolongation P_t (piecewise constant),
-// P = (I - w_p D^-1 A) P_t with w_p = 2 / rho, rho the Gershgorin bound of
-// the spectral radius of D^-1 A, the Galerkin operator P^T A P, and the
-// smoothed prolongation U = P - omega D^-1 A P used by the V-cycle with its
-// transpose; omega = min(0.9, 1.95 / rho) keeps omega times the spectral
-// radius below 2, so the damped-Jacobi smoother converges and the cycle is
-// positive definite.  (A CPU scan on the hard-cube potential matrix put
-// w_p in [1.3, 1.7] x 4 / (3 rho) and omega in [0.85, 0.95] on a plateau of
-// about 20 V-cycle-preconditioned CG steps per 1e-6 residual reduction,
-// against 23 with w_p = 4 / (3 rho), omega = 0.8.)  Leaves P.nlev = 0 (Jacobi only) when K_phi is small or the
-// coarsening stalls before the dense size.
+// Smoothed-aggregation multigrid hierarchy, built on the host in FP64 from
+// level 0's CSR matrix A.  Per level: greedy aggregates, tentative
+// prolongation P_t (piecewise constant), P = (I - w_p D^-1 A) P_t with
+// w_p = 2 / rho, rho the Gershgorin bound of the spectral radius of D^-1 A,
+// the Galerkin operator P^T A P, and the smoothed prolongation
+// U = P - omega D^-1 A P used by the V-cycle with its transpose;
+// omega = min(0.9, 1.95 / rho) keeps omega times the spectral radius below 2,
+// so the damped-Jacobi smoother converges and the cycle is positive
+// definite.  (A CPU scan on the hard-cube potential matrix put w_p in
+// [1.3, 1.7] x 4 / (3 rho) and omega in [0.85, 0.95] on a plateau of about
+// 20 V-cycle-preconditioned CG steps per 1e-6 residual reduction, against
+// 23 with w_p = 4 / (3 rho), omega = 0.8.)
+struct AmgHostLevel {
+    double omega;
+    HostCsr A, U, Ut;
+    std::vector<double> dinv;
+};
+
+struct AmgHost {
+    std::vector<AmgHostLevel> lev;       // smoothed levels
+    int nco = 0;                         // rows of the coarsest level
+    long long nnz_co = 0;                // its nonzeros
+    std::vector<double> ainv;            // [nco][nco] its inverse
+};
+
+// Returns false (no hierarchy: Jacobi only) when A is at most the dense
+// size, the coarsening stalls before it, or the coarsest operator is not
+// numerically positive definite.
+bool build_amg_host(HostCsr A, AmgHost& H) {
+    H = AmgHost();
+    if (A.n <= kCoarseDense) return false;
+    while ((int)H.lev.size() < MM_MAXLEV && A.n > kCoarseDense) {
+        std::vector<int> agg;
+        const int nc = aggregate(A, agg);
+        if (nc > A.n / 2) break;                          // coarsening stalled
+        std::vector<double> dinv(A.n, 1.0);
+        double rho = 0.0;
+        for (int i = 0; i < A.n; ++i) {
+            double d = 0.0, off = 0.0;
+            for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+                if (A.col[e] == i) d = A.val[e];
+                off += std::fabs(A.val[e]);
+            }
+            if (d > 0.0) {
+                dinv[i] = 1.0 / d;
+                rho = std::max(rho, off / d);
+            }
+        }
+        HostCsr Pt;
+        Pt.n = A.n;
+        Pt.m = nc;
+        Pt.ptr.resize(A.n + 1);
+        Pt.col = agg;
+        Pt.val.assign(A.n, 1.0);
+        for (int i = 0; i <= A.n; ++i) Pt.ptr[i] = i;
+        if (!(rho > 0.0)) rho = 2.0;
+        HostCsr Pm = minus_scaled_rows(Pt, 2.0 / rho, dinv, spgemm(A, Pt));
+        HostCsr AP = spgemm(A, Pm);
+        HostCsr Cc = spgemm(transpose(Pm), AP);
+        AmgHostLevel h;
+        h.omega = std::min(kAmgOmega, kAmgOmegaRho / rho);
+        h.U = minus_scaled_rows(Pm, h.omega, dinv, AP);
+        h.Ut = transpose(h.U);
+        h.dinv.swap(dinv);
+        h.A = std::move(A);
+        H.lev.push_back(std::move(h));
+        A = std::move(Cc);
+    }
+    if (H.lev.empty() || A.n > kCoarseDense || !dense_inverse(A, H.ainv)) {
+        H = AmgHost();
+        return false;
+    }
+    H.nco = A.n;
+    H.nnz_co = (long long)A.col.size();
+    return true;
+}
+
+// The V-cycle of the device (struct Level) on the host, FP64:
+// x = omega D^-1 b, rpre = b - A x, y_{l+1} = cycle(U^T b),
+// y = omega D^-1 (b + rpre) + U y_{l+1}; the coarsest level y = A^-1 b.
+void amg_host_vcycle(const AmgHost& H, size_t l, const double* b, double* y) {
+    if (l == H.lev.size()) {
+        const int n = H.nco;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += H.ainv[(size_t)i * n + j] * b[j];
+            y[i] = s;
+        }
+        return;
+    }
+    const AmgHostLevel& V = H.lev[l];
+    const int n = V.A.n, nc = V.U.m;
+    std::vector<double> x(n), rpre(n), bc(nc), yc(nc);
+    for (int i = 0; i < n; ++i) x[i] = V.omega * V.dinv[i] * b[i];
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (long long e = V.A.ptr[i]; e < V.A.ptr[i + 1]; ++e) s += V.A.val[e] * x[V.A.col[e]];
+        rpre[i] = b[i] - s;
+    }
+    for (int I = 0; I < nc; ++I) {
+        double s = 0.0;
+        for (long long e = V.Ut.ptr[I]; e < V.Ut.ptr[I + 1]; ++e) s += V.Ut.val[e] * b[V.Ut.col[e]];
+        bc[I] = s;
+    }
+    amg_host_vcycle(H, l + 1, bc.data(), yc.data());
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (long long e = V.U.ptr[i]; e < V.U.ptr[i + 1]; ++e) s += V.U.val[e] * yc[V.U.col[e]];
+        y[i] = V.omega * V.dinv[i] * (b[i] + rpre[i]) + s;
+    }
+}
+
+// The hierarchy of K_phi for the FP32 potential solve: built on the host
+// from the device SELL layout of level 0 (sptr/col/Kp), uploaded in FP32
+// (operators SELL-32, U^T CSR).  Leaves P.nlev = 0 (Jacobi only) when there
+// is none.
 int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& sptr, const std::vector<int>& col,
                     const double* Kp, long long nnz) {
     int rc;
@@ -509,57 +611,12 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
             A.ptr[r + 1] = (long long)A.col.size();
         }
     }
-    const long long nnz0 = (long long)A.col.size();
-    struct Host {
-        double omega;
-        HostCsr U, Ut;
-        std::vector<float> dinv;
-    };
-    std::vector<Host> host;
-    std::vector<HostCsr> ops;                             // A_l for l >= 1
-    while ((int)host.size() < MM_MAXLEV && A.n > kCoarseDense) {
-        std::vector<int> agg;
-        const int nc = aggregate(A, agg);
-        if (nc > A.n / 2) break;                          // coarsening stalled
-        std::vector<double> dinv(A.n, 1.0);
-        double rho = 0.0;
-        for (int i = 0; i < A.n; ++i) {
-            double d = 0.0, off = 0.0;
-            for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
-                if (A.col[e] == i) d = A.val[e];
-                off += std::fabs(A.val[e]);
-            }
-            if (d > 0.0) {
-                dinv[i] = 1.0 / d;
-                rho = std::max(rho, off / d);
-            }
-        }
-        HostCsr Pt;
-        Pt.n = A.n;
-        Pt.m = nc;
-        Pt.ptr.resize(A.n + 1);
-        Pt.col = agg;
-        Pt.val.assign(A.n, 1.0);
-        for (int i = 0; i <= A.n; ++i) Pt.ptr[i] = i;
-        if (!(rho > 0.0)) rho = 2.0;
-        HostCsr Pm = minus_scaled_rows(Pt, 2.0 / rho, dinv, spgemm(A, Pt));
-        HostCsr AP = spgemm(A, Pm);
-        HostCsr Cc = spgemm(transpose(Pm), AP);
-        Host h;
-        h.omega = std::min(kAmgOmega, kAmgOmegaRho / rho);
-        h.U = minus_scaled_rows(Pm, h.omega, dinv, AP);
-        h.Ut = transpose(h.U);
-        h.dinv.assign(dinv.begin(), dinv.end());
-        host.push_back(std::move(h));
-        A = std::move(Cc);
-        ops.push_back(A);
-    }
-    std::vector<float> ainv;
-    if (host.empty() || A.n > kCoarseDense || !dense_inverse(A, ainv)) return MM_OK;   // Jacobi only
-    const int L = (int)host.size();
+    AmgHost H;
+    if (!build_amg_host(std::move(A), H)) return MM_OK;   // Jacobi only
+    const int L = (int)H.lev.size();
     for (int l = 0; l < L; ++l) {
         mm::Level& V = P.lev[l];
-        const Host& h = host[l];
+        const AmgHostLevel& h = H.lev[l];
         V.n = h.U.n;
         V.nc = h.U.m;
         V.omega = (float)h.omega;
@@ -572,9 +629,10 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
             V.x = nullptr;
             V.y = P.pprec32;
         } else {
-            if ((rc = upload_sell(ctx, ops[l - 1], &V.sptr, &V.col, &V.val))) return rc;
+            if ((rc = upload_sell(ctx, h.A, &V.sptr, &V.col, &V.val))) return rc;
+            std::vector<float> df(h.dinv.begin(), h.dinv.end());
             float* d;
-            if ((rc = upload(ctx, &d, h.dinv.data(), h.dinv.size()))) return rc;
+            if ((rc = upload(ctx, &d, df.data(), df.size()))) return rc;
             V.dinv = d;
             if ((rc = dalloc(ctx, &V.b, V.n))) return rc;
             if ((rc = dalloc(ctx, &V.y, V.n))) return rc;
@@ -596,18 +654,22 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
         if ((rc = dalloc(ctx, &V.rpre, V.n))) return rc;
     }
     if ((rc = dalloc(ctx, &P.amg_x0, n0))) return rc;
-    float* a;
-    if ((rc = upload(ctx, &a, ainv.data(), ainv.size()))) return rc;
-    P.ainv = a;
-    P.nco = A.n;
-    if ((rc = dalloc(ctx, &P.bco, A.n))) return rc;
-    if ((rc = dalloc(ctx, &P.yco, A.n))) return rc;
+    {
+        std::vector<float> af(H.ainv.begin(), H.ainv.end());
+        float* a;
+        if ((rc = upload(ctx, &a, af.data(), af.size()))) return rc;
+        P.ainv = a;
+    }
+    P.nco = H.nco;
+    if ((rc = dalloc(ctx, &P.bco, H.nco))) return rc;
+    if ((rc = dalloc(ctx, &P.yco, H.nco))) return rc;
     P.nlev = L;
     P.amg_omega = P.lev[0].omega;
-    ctx->amg_nnz_a.push_back(nnz0);
-    for (const HostCsr& o : ops) ctx->amg_nnz_a.push_back((long long)o.col.size());
-    ctx->amg_nnz_a.back() = (long long)A.n * A.n;               // the dense inverse
-    for (const Host& h : host) ctx->amg_nnz_u.push_back((long long)h.U.col.size());
+    for (const AmgHostLevel& h : H.lev) {
+        ctx->amg_nnz_a.push_back((long long)h.A.col.size());
+        ctx->amg_nnz_u.push_back((long long)h.U.col.size());
+    }
+    ctx->amg_nnz_a.push_back((long long)H.nco * H.nco);        // the dense inverse
     return MM_OK;
 }
 
@@ -1229,6 +1291,34 @@ int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nn
         if (nnz_a) nnz_a[l] = ctx->amg_nnz_a[l];
         if (nnz_u && l < P.nlev) nnz_u[l] = ctx->amg_nnz_u[l];
     }
+    return MM_OK;
+}
+
+int mm_amg_host_apply(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, int32_t n_vec,
+                      const double* r, double* z, int32_t* n_levels, int64_t* rows, int32_t max_rows) {
+    if (n < 1 || n > INT32_MAX || !row_ptr || !col || !val || n_vec < 0 || (n_vec > 0 && (!r || !z)))
+        return MM_ERR_ARG;
+    if (row_ptr[0] != 0) return MM_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return MM_ERR_ARG;
+    HostCsr A;
+    A.n = A.m = (int)n;
+    A.ptr.assign(row_ptr, row_ptr + n + 1);
+    const long long nnz = A.ptr[n];
+    A.col.resize(nnz);
+    A.val.resize(nnz);
+    for (long long e = 0; e < nnz; ++e) {
+        if (col[e] < 0 || col[e] >= n) return MM_ERR_ARG;
+        A.col[e] = col[e];
+        A.val[e] = val[e];
+    }
+    AmgHost H;
+    const bool ok = build_amg_host(std::move(A), H);
+    const int L = ok ? (int)H.lev.size() : 0;
+    if (n_levels) *n_levels = L;
+    if (!ok) return MM_OK;
+    for (int l = 0; l <= L && rows && l < max_rows; ++l) rows[l] = (l < L) ? H.lev[l].A.n : H.nco;
+    for (int32_t v = 0; v < n_vec; ++v) amg_host_vcycle(H, 0, r + (size_t)v * n, z + (size_t)v * n);
     return MM_OK;
 }
 
