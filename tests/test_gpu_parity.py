@@ -231,3 +231,29 @@ def test_soft_cube_first_field_step(lib, prec):
     assert st["status"] == "ok" and r.status == "converged"
     assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
     assert np.abs(m - r.m).max() < 1e-5
+
+
+@pytest.mark.parametrize("psi_deg", [20.0, 45.0, 70.0])
+def test_stoner_wohlfarth_astroid_on_gpu(lib, psi_deg):
+    """The GPU minimiser on a single-domain particle (2 nm edge, far below
+    the exchange length; a cube has no shape anisotropy, so the stray field
+    of the uniform state does not move the switching field): the metastable
+    state from m = +z survives at 0.98 and is gone at 1.02 of the astroid
+    field 2K/(mu0 Ms) (cos^2/3 psi + sin^2/3 psi)^-3/2."""
+    Magnet, Params = lib[0], lib[1]
+    wl = synth.small_cube(n_mag=2, h=1e-9, Ms=1.28e6, A=7.7e-12, K1=4.3e6, axis=(0.0, 0.0, 1.0),
+                          m0=(0, 0, 1), box_factor=3.0)
+    psi = np.radians(psi_deg)
+    hsw = 2 * 4.3e6 / 1.28e6 * (np.cos(psi) ** (2 / 3) + np.sin(psi) ** (2 / 3)) ** -1.5
+    u = np.array([np.sin(psi), 0.0, -np.cos(psi)])
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    for f, switched in ((0.98, False), (1.02, True)):
+        mag.set_magnetization(wl.m0)
+        mag.set_field(f * hsw * u)
+        st = mag.minimize(Params(jmax=4))
+        assert st["status"] == "ok"
+        m = mag.get_magnetization()
+        mz = m[np.linalg.norm(m, axis=1) > 0, 2]
+        assert (mz.mean() < 0) == switched
+    mag.close()

@@ -77,6 +77,27 @@ def test_stoner_wohlfarth_switching_field(jmax):
         assert r.m[:, 2].std() < 1e-5
 
 
+@pytest.mark.parametrize("psi_deg", [15.0, 30.0, 45.0, 60.0, 75.0])
+def test_stoner_wohlfarth_astroid(psi_deg):
+    """The same single-domain particle with its easy axis along z and the
+    field reversed at angle psi from the axis: the metastable state reached
+    from m = +z must survive at 0.98 and be gone at 1.02 of the astroid
+    field h_sw(psi) = 2K/(mu0 Ms) (cos^2/3 psi + sin^2/3 psi)^-3/2."""
+    wl = synth.small_cube(n_mag=2, h=1e-9, Ms=1.28e6, A=7.7e-12, K1=4.3e6, axis=(0.0, 0.0, 1.0),
+                          m0=(0, 0, 1))
+    P = fem.assemble_workload(wl)
+    P.D = sp.csr_matrix(P.D.shape)          # magnetostatics off
+    psi = np.radians(psi_deg)
+    hsw = 2 * 4.3e6 / 1.28e6 * (np.cos(psi) ** (2 / 3) + np.sin(psi) ** (2 / 3)) ** -1.5
+    u = np.array([np.sin(psi), 0.0, -np.cos(psi)])
+    for f, switched in ((0.98, False), (1.02, True)):
+        m = np.tile([0.0, 0.0, 1.0], (P.n_mag, 1))
+        r = ncg.minimize(P, m, P.units.field_int(f * hsw * u), ncg.Params(jmax=4))
+        assert r.status == "converged"
+        assert (r.m[:, 2].mean() < 0) == switched
+        assert r.m[:, 2].std() < 1e-5
+
+
 def _soft_problem():
     wl = synth.small_cube(n_mag=3, h=2e-9, jitter=0.05, seed=9)
     return wl, fem.assemble_workload(wl)
