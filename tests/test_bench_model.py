@@ -1,0 +1,40 @@
+"""The algorithmic byte model bench.py divides by kernel time (no GPU):
+the multigrid V-cycle bytes against the per-level formula written out, and
+the precision forms' step bytes against their definitions."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+LEVELS = [{"rows": 1000, "nnz_a": 15000, "nnz_u": 9000},
+          {"rows": 40, "nnz_a": 1600, "nnz_u": 500},
+          {"rows": 3, "nnz_a": 9, "nnz_u": None}]
+
+
+def test_vcycle_bytes(bench):
+    # level 0: 8*15000 + 16*9000 + 28*1000 + 16*40; level 1 (last smoothed):
+    # 8*1600 + 16*500 + 28*40 + 8*3; dense coarsest 4*9 + 8*3
+    want = (8 * 15000 + 16 * 9000 + 28 * 1000 + 16 * 40) + (8 * 1600 + 16 * 500 + 28 * 40 + 8 * 3) + (4 * 9 + 8 * 3)
+    assert bench.vcycle_bytes(LEVELS) == want
+
+
+def test_step_bytes(bench):
+    sz = {"n_phi": 1000, "n_mag": 100, "nnz_phi": 15000, "nnz_mag": 1400}
+    st = {"mi": 20, "mr": 2, "evals": 3, "li": 4, "nli": 1}
+    base = bench.alg_bytes(dict(st, mi=0, mr=0), sz)
+    jac = bench.alg_bytes(st, sz) - base
+    assert jac == 18 * (8 * 15000 + 52 * 1000) + 2 * (12 * 15000 + 60 * 1000)
+    mg = bench.alg_bytes(st, sz, LEVELS) - base
+    vc = bench.vcycle_bytes(LEVELS)
+    assert mg == 18 * (8 * 15000 + 52 * 1000 + vc) + 2 * (12 * 15000 + 60 * 1000 + vc)
