@@ -214,18 +214,22 @@ def test_invalid_inputs(lib):
         mag.upload_mesh(wl.mesh.xyz, wl.mesh.tets, wl.mesh.region, air)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_soft_cube_first_field_step(lib, prec):
+@pytest.mark.parametrize("prec,amg", [(0, 0), (1, 0), (1, 1)])
+def test_soft_cube_first_field_step(lib, prec, amg):
     """Config 1 at full size (40 nm permalloy cube, 16^3 voxels, 29,791
     potential unknowns) from its seeded random start at +100 mT: the GPU
-    minimisation against the oracle's."""
+    minimisation (plain FP64, precision form with Jacobi and with the
+    multigrid preconditioner) against the oracle's."""
     Magnet, Params = lib
     wl = synth.soft_cube()
     mag, P = _setup(lib, wl)
     b = wl.fields[0]
     mag.set_magnetization(wl.m0)
     mag.set_field(b)
-    st = mag.minimize(Params(jmax=4, poisson_tol=1e-12, precision=prec))
+    if amg:
+        assert mag.amg_levels()
+    st = mag.minimize(Params(jmax=4, poisson_tol=1e-12, precision=prec, amg=amg,
+                             inner_tol=1e-3 if amg else 0.1))
     m = mag.get_magnetization()[P.mag_nodes]
     r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b), ncg.Params(jmax=4))
     assert st["status"] == "ok" and r.status == "converged"
