@@ -242,10 +242,12 @@ int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields,
  * and starts from zero on every call.  Size limit:
  * 11 n_mag + 6 n_phi doubles plus about 32 doubles per persistent block
  * must fit in 8 MiB (about n_phi <= 150,000 for a cube in a box twice its
- * size); larger problems return MM_ERR_ARG with the required size.  The
- * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current): make that first call
- * before any stream capture.  Every call shares the array and leaves its
+ * size); larger problems return MM_ERR_ARG with the required size.  Every
+ * call looks up the array's device address on the context's device
+ * (cudaGetSymbolAddress, with that device current; a device reset thus
+ * needs no special handling): make the first call on a device before any
+ * stream capture.  A zero or non-finite vector of m_dev on a magnetic node
+ * returns MM_ERR_NONFINITE.  Every call shares the array and leaves its
  * contents behind; calls that overlap on the GPU (other contexts or threads
  * on the same device) race on it.  Synchronises the context's stream. */
 int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, const mm_params* p,

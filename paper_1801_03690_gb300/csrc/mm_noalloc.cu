@@ -33,23 +33,20 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set-up once
-// per device, with that device current).
+// Device address of the scratch array on the current device, looked up on
+// every call with that device current (a cheap host call; a cached address
+// would go stale if the caller reset the device and made a new context).
 int scratch_address(int dev, double** out) {
     if (dev < 0 || dev >= kMaxDevices) return MM_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return MM_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = (double*)p;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return MM_ERR_CUDA;
     }
-    *out = g_scratch_addr[dev];
+    *out = (double*)p;
     return MM_OK;
 }
 
@@ -64,7 +61,6 @@ __global__ void k_noalloc_prep(int nm, const int* mag_nodes, const double* m_nod
         st->h[0] = h0;
         st->h[1] = h1;
         st->h[2] = h2;
-        *bad = 0;
     }
     if (i >= nm) return;
     const long long n = mag_nodes[i];
@@ -181,9 +177,12 @@ extern "C" int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, cons
     const double hs = 1.0 / (kMu0 * v.Mref);
     int* bad = (int*)(S + o_bad);
     cudaError_t e;
-    // clear what must start at zero: barrier words, error flag, potential
+    // clear what must start at zero: barrier words, error flag, the flag of
+    // bad input vectors (cleared on the stream before the kernel that sets
+    // it: blocks of one launch run in no fixed order), potential
     if ((e = cudaMemsetAsync(Q.bar, 0, 64 * sizeof(unsigned), st)) != cudaSuccess ||
         (e = cudaMemsetAsync(Q.err, 0, sizeof(int), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(bad, 0, sizeof(int), st)) != cudaSuccess ||
         (e = cudaMemsetAsync(Q.phi, 0, np * sizeof(double), st)) != cudaSuccess)
         return mm::ctx_fail(ctx, MM_ERR_CUDA, cudaGetErrorString(e));
     const int nb = (int)((nm + 255) / 256);

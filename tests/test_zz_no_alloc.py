@@ -76,3 +76,38 @@ def test_noalloc_rejects_problems_beyond_its_array():
     assert rc == -1
     assert "MiB" in lib.mm_last_error(mag._h).decode()
     mag.close()
+
+
+def test_noalloc_rejects_zero_and_nonfinite_vectors():
+    """A zero vector or a NaN on one of the last magnetic nodes is reported
+    as MM_ERR_NONFINITE on every call (the flag is cleared on the stream
+    before the launch that may set it), and a valid call after them works."""
+    import torch
+    from paper_1801_03690_gb300 import Magnet, Params
+    from paper_1801_03690_gb300 import _lib
+
+    lib = _lib.load()
+    wl = _hard(6)
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    mag.set_field([0.1, 0.0, -0.5])
+    pc = Params(poisson_tol=1e-12).to_c()
+    mag_nodes = np.nonzero(np.isin(np.arange(wl.mesh.n_nodes),
+                                   np.unique(wl.mesh.tets[wl.mesh.region == 1])))[0]
+    energy_dev = torch.zeros(5, dtype=torch.float64, device="cuda")
+    for bad in ("zero", "nan"):
+        m = wl.m0.copy()
+        node = mag_nodes[-1] if bad == "zero" else mag_nodes[-2]
+        m[node] = 0.0 if bad == "zero" else np.nan
+        m_dev = torch.tensor(m, dtype=torch.float64, device="cuda")
+        for _ in range(4):
+            rc = lib.mm_energy_gradient_noalloc(mag._h, C.c_void_p(m_dev.data_ptr()), C.byref(pc), None, 0,
+                                                C.c_void_p(energy_dev.data_ptr()))
+            assert rc == -5, (bad, rc)
+    m_dev = torch.tensor(wl.m0, dtype=torch.float64, device="cuda")
+    rc = lib.mm_energy_gradient_noalloc(mag._h, C.c_void_p(m_dev.data_ptr()), C.byref(pc), None, 0,
+                                        C.c_void_p(energy_dev.data_ptr()))
+    assert rc == 0, lib.mm_last_error(mag._h).decode()
+    F_ref, _ = mag.energy(wl.m0, Params(poisson_tol=1e-12))
+    assert float(energy_dev[0].item()) == pytest.approx(F_ref, rel=1e-10)
+    mag.close()
