@@ -125,7 +125,12 @@ const char* mm_last_error(const mm_ctx* ctx);
  * and assemble (on the GPU) every operator of Eq. (energy): the exchange
  * stiffness, the lumped anisotropy blocks and Ms weights, the scalar-
  * potential stiffness over magnet + air with phi = 0 on the outer surface of
- * the mesh, and the divergence coupling.  Sec. 2.2 and 3.1.
+ * the mesh, and the divergence coupling.  Sec. 2.2 and 3.1.  Couplings of
+ * the potential stiffness that vanish in exact arithmetic but are assembled
+ * as rounding residues (|a_ij| <= 1e-12 sqrt(a_ii a_jj); the face and body
+ * diagonals of a rectilinear Kuhn lattice) are dropped: a product with the
+ * stored operator differs from the assembled one by less than 1e-12
+ * relative.
  *   xyz    [n_nodes][3] coordinates, m
  *   tets   [n_tets][4] node ids (either orientation; degenerate -> MM_ERR_MESH)
  *   region [n_tets] labels in [0, n_regions)
@@ -156,7 +161,11 @@ int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nn
  * caller keeps ownership), and apply its V-cycle in FP64 to n_vec vectors
  * r [n_vec][n], writing z [n_vec][n].  This is the cycle the solver kernel
  * runs in FP32 (same set-up, same algebra), exposed so that the set-up can
- * be checked without a GPU.  *n_levels and rows as in mm_amg_info; when
+ * be checked without a GPU.  Level 0 is aggregated on A's stored pattern
+ * (values ignored) and computed with A without its rounding residues
+ * (off-diagonal |a_ij| <= 1e-12 sqrt(a_ii a_jj)); every coarser level is the
+ * Galerkin operator without its residues, columns ascending, aggregated on
+ * its own pattern.  *n_levels and rows as in mm_amg_info; when
  * there is no hierarchy (n <= 1536, or the coarsening stalls) *n_levels = 0
  * and z is left untouched.  MM_ERR_ARG for null pointers, n < 1,
  * decreasing row_ptr or a column outside [0, n). */

@@ -156,6 +156,16 @@ int dalloc(mm_ctx* ctx, T** p, size_t count) {
     return MM_OK;
 }
 
+// Free one device buffer of the mesh (allocated by dalloc).
+void dfree(mm_ctx* ctx, const void* p) {
+    for (size_t k = 0; k < ctx->allocs.size(); ++k)
+        if (ctx->allocs[k] == p) {
+            cudaFree(ctx->allocs[k]);
+            ctx->allocs.erase(ctx->allocs.begin() + k);
+            return;
+        }
+}
+
 void free_mesh(mm_ctx* ctx) {
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
@@ -243,10 +253,11 @@ struct HostCsr {
     std::vector<double> val;
 };
 
-// Greedy aggregation of the matrix graph: (1) a node whose neighbours are
-// all free starts an aggregate with them; (2) remaining nodes join the
-// aggregate of their first aggregated neighbour; (3) the rest become
-// singletons.  Returns the number of aggregates.
+// Greedy aggregation of the matrix graph (every stored entry is an edge,
+// whatever its value): (1) a node whose neighbours are all free starts an
+// aggregate with them; (2) remaining nodes join the aggregate of their
+// first aggregated neighbour; (3) the rest become singletons.  Returns the
+// number of aggregates.
 int aggregate(const HostCsr& A, std::vector<int>& agg) {
     const int n = A.n;
     agg.assign(n, -1);
@@ -255,11 +266,10 @@ int aggregate(const HostCsr& A, std::vector<int>& agg) {
         if (agg[i] >= 0) continue;
         bool free_nb = true;
         for (long long e = A.ptr[i]; e < A.ptr[i + 1] && free_nb; ++e)
-            if (A.col[e] != i && A.val[e] != 0.0 && agg[A.col[e]] >= 0) free_nb = false;
+            if (A.col[e] != i && agg[A.col[e]] >= 0) free_nb = false;
         if (!free_nb) continue;
         agg[i] = na;
-        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
-            if (A.val[e] != 0.0) agg[A.col[e]] = na;
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) agg[A.col[e]] = na;
         ++na;
     }
     std::vector<int> first(agg);
@@ -267,7 +277,7 @@ int aggregate(const HostCsr& A, std::vector<int>& agg) {
         if (first[i] >= 0) continue;
         for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
             const int j = A.col[e];
-            if (j != i && A.val[e] != 0.0 && first[j] >= 0) {
+            if (j != i && first[j] >= 0) {
                 agg[i] = first[j];
                 break;
             }
@@ -359,9 +369,11 @@ HostCsr minus_scaled_rows(const HostCsr& B, double s, const std::vector<double>&
     return C;
 }
 
-// SELL-32 layout of a host CSR (values as float); padding entries carry
-// value 0 and their own row as column where that is a column of A, else 0.
-void csr_to_sell(const HostCsr& A, std::vector<long long>& sptr, std::vector<int>& col, std::vector<float>& val) {
+// SELL-32 layout of a host CSR (values converted to V); padding entries
+// carry value 0 and their own row as column where that is a column of A,
+// else 0.
+template <class V>
+void csr_to_sell(const HostCsr& A, std::vector<long long>& sptr, std::vector<int>& col, std::vector<V>& val) {
     const long long n = A.n, ns = (n + 31) / 32;
     sptr.assign(ns + 1, 0);
     for (long long s = 0; s < ns; ++s) {
@@ -370,7 +382,7 @@ void csr_to_sell(const HostCsr& A, std::vector<long long>& sptr, std::vector<int
         sptr[s + 1] = sptr[s] + 32 * w;
     }
     col.assign(sptr[ns], 0);
-    val.assign(sptr[ns], 0.0f);
+    val.assign(sptr[ns], V(0));
     for (long long s = 0; s < ns; ++s) {
         const long long w = (sptr[s + 1] - sptr[s]) / 32;
         for (int l = 0; l < 32; ++l) {
@@ -379,13 +391,57 @@ void csr_to_sell(const HostCsr& A, std::vector<long long>& sptr, std::vector<int
                 const long long e = sptr[s] + 32 * k + l;
                 if (r < n && k < A.ptr[r + 1] - A.ptr[r]) {
                     col[e] = A.col[A.ptr[r] + k];
-                    val[e] = (float)A.val[A.ptr[r] + k];
+                    val[e] = (V)A.val[A.ptr[r] + k];
                 } else {
                     col[e] = (r < A.m) ? (int)r : 0;   // padding: a valid column, value 0
                 }
             }
         }
     }
+}
+
+// Entries that are zero in exact arithmetic but not in floating point.
+// On a rectilinear (uniform or graded) Kuhn lattice the P1 Laplacian
+// couples a node only to its six axis neighbours: the couplings along face
+// and body diagonals are exactly zero, yet the assembled sums of b_i.b_j
+// leave rounding residues of ~1e-17 relative to the diagonal.  They are
+// dropped from the operators the potential solve applies; a coupling kept
+// on a general mesh is above 1e-7 relative (jittered lattices), and dropping
+// one below the threshold changes a product by less than 1e-12 relative.
+constexpr double kNoiseRel = 1e-12;
+
+// A without its off-diagonal entries a_ij with |a_ij| <= kNoiseRel *
+// sqrt(|a_ii a_jj|) (square A), columns ascending within each row (the
+// greedy aggregation breaks ties by storage order, so the order is fixed).
+HostCsr prune_noise(const HostCsr& A) {
+    std::vector<double> dg(A.n, 0.0);
+    for (int i = 0; i < A.n; ++i)
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
+            if (A.col[e] == i) dg[i] = std::fabs(A.val[e]);
+    HostCsr B;
+    B.n = A.n;
+    B.m = A.m;
+    B.ptr.assign(A.n + 1, 0);
+    B.col.reserve(A.col.size());
+    B.val.reserve(A.val.size());
+    std::vector<std::pair<int, double>> row;
+    for (int i = 0; i < A.n; ++i) {
+        row.clear();
+        for (long long e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+            const int j = A.col[e];
+            if (j != i && !(std::fabs(A.val[e]) > kNoiseRel * std::sqrt(dg[i] * dg[j]))) continue;
+            row.emplace_back(j, A.val[e]);
+        }
+        std::sort(row.begin(), row.end(), [](const std::pair<int, double>& a, const std::pair<int, double>& b) {
+            return a.first < b.first;
+        });
+        for (const auto& q : row) {
+            B.col.push_back(q.first);
+            B.val.push_back(q.second);
+        }
+        B.ptr[i + 1] = (long long)B.col.size();
+    }
+    return B;
 }
 
 // Inverse of a small SPD matrix, FP64, row-major:
@@ -468,7 +524,11 @@ constexpr double kAmgOmega = 0.9;       // Jacobi damping of the smoother, at mo
 constexpr double kAmgOmegaRho = 1.95;   // ... 1.95 / rho (rho >= the spectral radius of D^-1 A)
 
 // Smoothed-aggregation multigrid hierarchy, built on the host in FP64 from
-// level 0's CSR matrix A.  Per level: greedy aggregates, tentative
+// level 0's CSR matrix A.  Level 0 aggregates on A's stored pattern (the
+// mesh graph: values ignored, so rounding cannot change the aggregates) and
+// computes with A without its rounding residues (prune_noise); every
+// coarser level is the Galerkin operator without its residues, aggregated
+// on its own pattern.  Per level: greedy aggregates, tentative
 // prolongation P_t (piecewise constant), P = (I - w_p D^-1 A) P_t with
 // w_p = 2 / rho, rho the Gershgorin bound of the spectral radius of D^-1 A,
 // the Galerkin operator P^T A P, and the smoothed prolongation
@@ -500,8 +560,9 @@ bool build_amg_host(HostCsr A, AmgHost& H) {
     if (A.n <= kCoarseDense) return false;
     while ((int)H.lev.size() < MM_MAXLEV && A.n > kCoarseDense) {
         std::vector<int> agg;
-        const int nc = aggregate(A, agg);
+        const int nc = aggregate(A, agg);                 // on the stored pattern
         if (nc > A.n / 2) break;                          // coarsening stalled
+        if (H.lev.empty()) A = prune_noise(A);            // level 0: numerics without residues
         std::vector<double> dinv(A.n, 1.0);
         double rho = 0.0;
         for (int i = 0; i < A.n; ++i) {
@@ -533,7 +594,7 @@ bool build_amg_host(HostCsr A, AmgHost& H) {
         h.dinv.swap(dinv);
         h.A = std::move(A);
         H.lev.push_back(std::move(h));
-        A = std::move(Cc);
+        A = prune_noise(Cc);                              // coarse operator without residues
     }
     if (H.lev.empty() || A.n > kCoarseDense || !dense_inverse(A, H.ainv)) {
         H = AmgHost();
@@ -580,11 +641,11 @@ void amg_host_vcycle(const AmgHost& H, size_t l, const double* b, double* y) {
 }
 
 // The hierarchy of K_phi for the FP32 potential solve: built on the host
-// from the device SELL layout of level 0 (sptr/col/Kp), uploaded in FP32
-// (operators SELL-32, U^T CSR).  Leaves P.nlev = 0 (Jacobi only) when there
-// is none.
-int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& sptr, const std::vector<int>& col,
-                    const double* Kp, long long nnz) {
+// from A, level 0's operator as assembled (before prune_noise; level 0 of
+// the hierarchy is its pruned form, which the device holds as P.Kp32),
+// uploaded in FP32 (operators SELL-32, U^T CSR).  Leaves P.nlev = 0
+// (Jacobi only) when there is none.
+int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
     int rc;
     P.nlev = 0;
     P.nco = 0;
@@ -593,24 +654,6 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, const std::vector<long long>& s
     ctx->amg_nnz_u.clear();
     const int n0 = P.nphi;
     if (n0 <= kCoarseDense) return MM_OK;
-    HostCsr A;
-    A.n = A.m = n0;
-    A.ptr.assign(n0 + 1, 0);
-    {
-        std::vector<double> kp(nnz);
-        CK_CUDA(cudaStreamSynchronize(ctx->stream));
-        CK_CUDA(cudaMemcpy(kp.data(), Kp, nnz * sizeof(double), cudaMemcpyDeviceToHost));
-        for (int r = 0; r < n0; ++r) {
-            const long long s = r / 32, w = (sptr[s + 1] - sptr[s]) / 32;
-            for (long long k = 0; k < w; ++k) {
-                const long long e = sptr[s] + 32 * k + (r % 32);
-                if (kp[e] == 0.0) continue;               // SELL padding
-                A.col.push_back(col[e]);
-                A.val.push_back(kp[e]);
-            }
-            A.ptr[r + 1] = (long long)A.col.size();
-        }
-    }
     AmgHost H;
     if (!build_amg_host(std::move(A), H)) return MM_OK;   // Jacobi only
     const int L = (int)H.lev.size();
@@ -1070,7 +1113,7 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     build_sell(prow, p_sptr, p_col, nnzp_true);
     mrow.clear();
     prow.clear();
-    const long long nnzm = m_sptr.back(), nnzp = p_sptr.back();
+    const long long nnzm = m_sptr.back(), nnzp_asm = p_sptr.back();
 
     // ---- device upload and assembly
     int rc;
@@ -1111,7 +1154,7 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     if ((rc = dalloc(ctx, &CK, 6 * (size_t)nm))) return rc;
     if ((rc = dalloc(ctx, &w, nm))) return rc;
     if ((rc = dalloc(ctx, &dinvA, nm))) return rc;
-    if ((rc = dalloc(ctx, &Kp, nnzp))) return rc;
+    if ((rc = dalloc(ctx, &Kp, nnzp_asm))) return rc;
     if ((rc = dalloc(ctx, &dinvP, nphi))) return rc;
     CK_CUDA(cudaMemset(ctx->d_flag, 0, sizeof(int)));
     mm::k_tet_geometry<<<nblk(T), 256, 0, ctx->stream>>>(T, d_xyz, d_tets, d_vol, d_grad, ctx->d_flag);
@@ -1164,6 +1207,40 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
         free_mesh(ctx);
         return fail(ctx, MM_ERR_MESH, "assembly failed (code %d)", bad);
     }
+    // ---- the potential stiffness without its rounding residues
+    // (prune_noise): download, compact, upload again in SELL-32
+    HostCsr Kfull;
+    {
+        std::vector<double> kp(nnzp_asm);
+        CK_CUDA(cudaMemcpy(kp.data(), Kp, nnzp_asm * sizeof(double), cudaMemcpyDeviceToHost));
+        Kfull.n = Kfull.m = nphi;
+        Kfull.ptr.assign(nphi + 1, 0);
+        Kfull.col.reserve(nnzp_true);
+        Kfull.val.reserve(nnzp_true);
+        for (int r = 0; r < nphi; ++r) {
+            const long long sl = r / 32, w = (p_sptr[sl + 1] - p_sptr[sl]) / 32;
+            for (long long k = 0; k < w; ++k) {
+                const long long e = p_sptr[sl] + 32 * k + (r % 32);
+                if (p_col[e] == r && kp[e] == 0.0) continue;   // SELL padding
+                Kfull.col.push_back(p_col[e]);
+                Kfull.val.push_back(kp[e]);
+            }
+            Kfull.ptr[r + 1] = (long long)Kfull.col.size();
+        }
+    }
+    {
+        const HostCsr Kpr = prune_noise(Kfull);
+        std::vector<double> v;
+        csr_to_sell(Kpr, p_sptr, p_col, v);
+        dfree(ctx, d_psp);
+        dfree(ctx, d_pcol);
+        dfree(ctx, Kp);
+        if ((rc = upload(ctx, &d_psp, p_sptr.data(), p_sptr.size()))) return rc;
+        if ((rc = upload(ctx, &d_pcol, p_col.data(), p_col.size()))) return rc;
+        if ((rc = upload(ctx, &Kp, v.data(), v.size()))) return rc;
+        nnzp_true = (long long)Kpr.col.size();
+    }
+    const long long nnzp = p_sptr.back();
     P.m_sptr = d_msp;
     P.m_col = d_mcol;
     P.KA = KA;
@@ -1219,7 +1296,7 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
             CK_CUDA(cudaMemsetAsync(f, 0, nphi * sizeof(float), ctx->stream));
     }
     // aggregation multigrid hierarchy of K_phi for the FP32 potential solve
-    if ((rc = build_hierarchy(ctx, P, p_sptr, p_col, Kp, nnzp))) return rc;
+    if ((rc = build_hierarchy(ctx, P, std::move(Kfull)))) return rc;
     if ((rc = dalloc(ctx, &P.partials, 2 * (size_t)MM_MAXRED * ctx->blocks))) return rc;
     if ((rc = dalloc(ctx, &P.bar, 64))) return rc;
     if ((rc = dalloc(ctx, &P.err, 1))) return rc;

@@ -6,12 +6,13 @@ the minimisation method (no finite-element assembly, no energies, no solvers),
 so both the CUDA path and the CPU oracle may use it without sharing any of the
 method's code.
 """
-from .mesh import Mesh, kuhn_lattice, cube_in_box, jitter_nodes, voronoi_regions
+from .mesh import Mesh, kuhn_lattice, cube_in_box, jitter_nodes, voronoi_regions, grain_patches
 from .workloads import (Workload, soft_cube, hard_cube, polycrystal_cube,
                         small_cube, random_unit_vectors, cone_axes, platelet,
-                        platelet_batch)
+                        platelet_batch, graded_cube_in_box, large_polycrystal)
 
 __all__ = ["Mesh", "kuhn_lattice", "cube_in_box", "jitter_nodes",
-           "voronoi_regions", "Workload", "soft_cube", "hard_cube",
+           "voronoi_regions", "grain_patches", "Workload", "soft_cube", "hard_cube",
            "polycrystal_cube", "small_cube", "random_unit_vectors",
-           "cone_axes", "platelet", "platelet_batch"]
+           "cone_axes", "platelet", "platelet_batch",
+           "graded_cube_in_box", "large_polycrystal"]

@@ -139,6 +139,18 @@ def jitter_nodes(mesh, amp, seed):
                 spacing=mesh.spacing, meta=dict(mesh.meta, jitter=amp, jitter_seed=seed))
 
 
+def _two_nearest(points, seeds):
+    """Indices of the nearest and second-nearest seed of every point (a k-d
+    tree query) and the squared distances to them."""
+    from scipy.spatial import cKDTree
+    _, idx = cKDTree(seeds).query(points, k=2, workers=-1)
+    a = idx[:, 0].astype(np.int64)
+    b = idx[:, 1].astype(np.int64)
+    da = ((points - seeds[a]) ** 2).sum(-1)
+    db = ((points - seeds[b]) ** 2).sum(-1)
+    return a, b, da, db
+
+
 def voronoi_regions(mesh, n_grains, lo, hi, gb_thickness, seed, magnet_region=1):
     """Split the tetrahedra labelled `magnet_region` into Voronoi grains around
     n_grains seeds uniform in the box [lo, hi]^3.  A tetrahedron whose
@@ -147,20 +159,40 @@ def voronoi_regions(mesh, n_grains, lo, hi, gb_thickness, seed, magnet_region=1)
     1..n_grains, boundary phase n_grains+1, others unchanged."""
     rng = np.random.default_rng(seed)
     seeds = rng.uniform(lo, hi, size=(n_grains, 3))
-    cen = mesh.xyz[mesh.tets].mean(axis=1)
-    region = mesh.region.copy()
     sel = np.nonzero(mesh.region == magnet_region)[0]
-    c = cen[sel]
-    d2 = ((c[:, None, :] - seeds[None, :, :]) ** 2).sum(-1)
-    order = np.argsort(d2, axis=1)
-    a = order[:, 0]
-    b = order[:, 1]
-    da = d2[np.arange(len(sel)), a]
-    db = d2[np.arange(len(sel)), b]
+    c = mesh.xyz[mesh.tets[sel]].mean(axis=1)
+    a, b, da, db = _two_nearest(c, seeds)
     sep = np.linalg.norm(seeds[a] - seeds[b], axis=1)
     dist_plane = (db - da) / (2.0 * sep)
     lab = (a + 1).astype(np.int32)
     lab[dist_plane < 0.5 * gb_thickness] = n_grains + 1
+    region = mesh.region.copy()
     region[sel] = lab
     return Mesh(xyz=mesh.xyz, tets=mesh.tets, region=region, shape=mesh.shape,
                 spacing=mesh.spacing, meta=dict(mesh.meta, grains=n_grains, grain_seed=seed)), seeds
+
+
+def grain_patches(mesh, n_grains, patches_per_grain, seed):
+    """Divide every grain (labels 1..n_grains) into patches_per_grain
+    sub-regions: patch centres are the centroids of tetrahedra of the grain
+    drawn without replacement (seeded), and every tetrahedron of the grain
+    joins its nearest centre.  Returns (patch index in [0, patches) per
+    tetrahedron, -1 outside the grains)."""
+    rng = np.random.default_rng(seed)
+    patch = np.full(mesh.n_tets, -1, dtype=np.int32)
+    order = np.argsort(mesh.region, kind="stable")
+    bounds = np.searchsorted(mesh.region[order], np.arange(1, n_grains + 2))
+    for g in range(n_grains):
+        idx = order[bounds[g]:bounds[g + 1]]
+        if idx.size == 0:
+            continue
+        k = min(patches_per_grain, idx.size)
+        cen = mesh.xyz[mesh.tets[idx]].mean(axis=1)
+        centres = cen[rng.choice(idx.size, size=k, replace=False)]
+        if k == 1:
+            patch[idx] = 0
+            continue
+        from scipy.spatial import cKDTree
+        _, nearest = cKDTree(centres).query(cen, k=1, workers=-1)
+        patch[idx] = nearest.astype(np.int32)
+    return patch

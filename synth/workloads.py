@@ -11,7 +11,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .mesh import Mesh, cube_in_box, jitter_nodes, voronoi_regions
+from .mesh import Mesh, cube_in_box, jitter_nodes, voronoi_regions, grain_patches, kuhn_lattice
 
 MU0 = 4e-7 * np.pi
 
@@ -133,6 +133,72 @@ def polycrystal_cube(n_mag=114, edge=200e-9, box_factor=2.0, n_grains=27, seed=3
     return Workload(name=f"polycrystal_{n_grains}g_{n_mag}", mesh=mesh, materials=mats,
                     fields=fields, m0=m0,
                     meta={"edge": edge, "h": h, "seed": seed, "grain_seeds": seeds})
+
+
+def graded_cube_in_box(n_mag, edge, box_factor=2.0, ratio=1.06):
+    """A cube magnet of n_mag voxels per edge (spacing h = edge / n_mag)
+    centred in a cubic air box of box_factor x edge, on a tensor lattice that
+    is uniform over the magnet and graded outside it (each air cell `ratio`
+    times the previous one).  Region 1 = magnet, region 0 = air."""
+    h = edge / n_mag
+    ax = _graded_axis(edge / 2.0, h, box_factor * edge / 2.0, ratio)
+    xyz, tets, vox = kuhn_lattice(ax, ax, ax)
+    nv = len(ax) - 1
+    lo = (nv - n_mag) // 2
+    vi = vox % nv
+    vj = (vox // nv) % nv
+    vk = vox // (nv * nv)
+    inside = ((vi >= lo) & (vi < lo + n_mag) & (vj >= lo) & (vj < lo + n_mag)
+              & (vk >= lo) & (vk < lo + n_mag))
+    return Mesh(xyz=xyz, tets=tets, region=inside.astype(np.int32), shape=(nv + 1,) * 3, spacing=h,
+                meta={"n_mag": n_mag, "graded_ratio": ratio, "n_box": nv})
+
+
+def large_polycrystal(n_mag=149, edge=250e-9, box_factor=2.0, ratio=1.06, n_grains=125, seed=5,
+                      gb_thickness=2e-9, cone_deg=15.0, n_fields=60, b_stop=-8.0, gb_factor=0.4,
+                      patches_per_grain=0, k1_sigma=0.05):
+    """Large polycrystalline Nd2Fe14B cube: n_mag^3 voxels (6 tets each;
+    149^3 voxels = 19.8 M magnet tets, 150^3 = 3.375 M magnetic nodes),
+    n_grains Voronoi grains with easy axes uniform in a cone about +z, a
+    grain-boundary phase of thickness gb_thickness with Ms and K1 at
+    gb_factor, in a graded air box of box_factor x edge; m0 = +z; field along
+    -z from 0 to b_stop tesla in n_fields values.  With patches_per_grain > 0
+    every grain is split into that many patches whose K1 is drawn from a
+    Gaussian of mean K1 and relative standard deviation k1_sigma (the
+    nanocrystalline magnet of Sec. 3.4: local changes of the composition)."""
+    mesh = graded_cube_in_box(n_mag, edge, box_factor, ratio)
+    half = edge / 2.0
+    mesh, seeds = voronoi_regions(mesh, n_grains, -half, half, gb_thickness, seed)
+    axes = cone_axes(n_grains, cone_deg, seed + 1000)
+    rows = [(0, 0, 0, 0, 0, 1)]
+    Ms, A, K1 = ND2FE14B["Ms"], ND2FE14B["A"], ND2FE14B["K1"]
+    if patches_per_grain > 0:
+        patch = grain_patches(mesh, n_grains, patches_per_grain, seed + 2000)
+        rng = np.random.default_rng(seed + 3000)
+        k1 = K1 * (1.0 + k1_sigma * rng.standard_normal((n_grains, patches_per_grain)))
+        region = mesh.region.copy()
+        g = region - 1
+        isg = (region >= 1) & (region <= n_grains)
+        region[isg] = 1 + g[isg] * patches_per_grain + patch[isg]
+        region[mesh.region == n_grains + 1] = 1 + n_grains * patches_per_grain
+        for gi in range(n_grains):
+            for q in range(patches_per_grain):
+                rows.append((Ms, A, k1[gi, q], *axes[gi]))
+        mesh = Mesh(xyz=mesh.xyz, tets=mesh.tets, region=region, shape=mesh.shape, spacing=mesh.spacing,
+                    meta=dict(mesh.meta, patches_per_grain=patches_per_grain, k1_sigma=k1_sigma))
+    else:
+        for gi in range(n_grains):
+            rows.append((Ms, A, K1, *axes[gi]))
+    rows.append((gb_factor * Ms, A, gb_factor * K1, 0, 0, 1))
+    mats = _material_table(rows)
+    b = np.linspace(0.0, b_stop, n_fields)
+    fields = np.stack([np.zeros_like(b), np.zeros_like(b), b], axis=1)
+    m0 = np.tile([0.0, 0.0, 1.0], (mesh.n_nodes, 1))
+    tag = f"_p{patches_per_grain}" if patches_per_grain else ""
+    return Workload(name=f"large_polycrystal_{n_grains}g_{n_mag}{tag}", mesh=mesh, materials=mats,
+                    fields=fields, m0=m0,
+                    meta={"edge": edge, "h": edge / n_mag, "seed": seed, "grain_seeds": seeds,
+                          "graded_ratio": ratio, "n_mag": n_mag})
 
 
 def _graded_axis(half_mag, h, half_box, ratio):

@@ -31,6 +31,13 @@ def K16():
     return _K(synth.hard_cube(n_mag=16))
 
 
+@pytest.fixture(scope="module")
+def Kgraded():
+    """Potential stiffness of an unjittered polycrystal in a graded air box:
+    its face- and body-diagonal couplings are rounding residues."""
+    return _K(synth.large_polycrystal(n_mag=20, edge=40e-9, n_grains=6))
+
+
 def _apply(lib, A, R):
     return lib[0](A.indptr, A.indices, A.data, R)
 
@@ -68,10 +75,24 @@ def _aggregate(A):
     return agg, na
 
 
+def _prune(A, rel=1e-12):
+    """A without the off-diagonal entries |a_ij| <= rel sqrt(|a_ii a_jj|):
+    couplings that vanish in exact arithmetic (the face and body diagonals
+    of a rectilinear Kuhn lattice) but were assembled as rounding residues."""
+    C = A.tocoo()
+    d = np.abs(A.diagonal())
+    keep = (C.row == C.col) | (np.abs(C.data) > rel * np.sqrt(d[C.row] * d[C.col]))
+    return sp.csr_matrix((C.data[keep], (C.row[keep], C.col[keep])), shape=A.shape)
+
+
 def _hierarchy(A, n_dense=1536):
     levels = []
     while A.shape[0] > n_dense:
-        agg, nc = _aggregate(A)
+        agg, nc = _aggregate(A)            # on the stored pattern
+        if nc > A.shape[0] // 2:
+            break
+        if not levels:
+            A = _prune(A)                  # level 0: numerics without the residues
         d = A.diagonal()
         rho = (abs(A).sum(axis=1).A1 / d).max()
         Dinv = sp.diags(1.0 / d)
@@ -79,7 +100,7 @@ def _hierarchy(A, n_dense=1536):
         P = (Pt - (2.0 / rho) * (Dinv @ (A @ Pt))).tocsr()
         omega = min(0.9, 1.95 / rho)
         levels.append((A, P, 1.0 / d, omega))
-        A = (P.T @ A @ P).tocsr()
+        A = _prune((P.T @ A @ P).tocsr())  # coarse operator without residues
     return levels, np.linalg.inv(A.toarray())
 
 
@@ -164,3 +185,26 @@ def test_rejects_bad_csr(lib):
     bad[5] = 2000
     with pytest.raises(lib[1]):
         lib[0](A.indptr, bad, A.data, np.ones((1, 2000)))
+
+
+def test_residues_are_pruned_and_cycle_matches(lib, Kgraded):
+    """On a rectilinear Kuhn lattice about half of the stored couplings are
+    rounding residues (below 1e-15 of the diagonal); the hierarchy's
+    numerics drop them (the aggregates still come from the stored pattern)
+    and the cycle agrees with the restatement that does the same."""
+    P = _prune(Kgraded)
+    d = np.abs(Kgraded.diagonal())
+    C = Kgraded.tocoo()
+    off = C.row != C.col
+    rel = np.abs(C.data[off]) / np.sqrt(d[C.row[off]] * d[C.col[off]])
+    assert (rel <= 1e-12).sum() > 0.3 * off.sum()
+    assert rel[rel <= 1e-12].max() < 1e-15 and rel[rel > 1e-12].min() > 1e-3
+    rng = np.random.default_rng(6)
+    R = rng.standard_normal((2, Kgraded.shape[0]))
+    Z, levels = _apply(lib, Kgraded, R)
+    lv, Ainv = _hierarchy(Kgraded)
+    assert [L[0].shape[0] for L in lv] + [Ainv.shape[0]] == levels
+    assert lv[0][0].nnz == P.nnz < 0.7 * Kgraded.nnz
+    for r, z in zip(R, Z):
+        ref = _vcycle(lv, Ainv, r)
+        assert np.abs(z - ref).max() <= 1e-10 * np.abs(ref).max()
