@@ -233,6 +233,20 @@ int mm_potential_matvec(mm_ctx* ctx, const double* v, double* out);
 int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields,
                    const mm_params* p, mm_stats* stats_out);
 
+/* Coercive field of a demagnetisation curve (Sec. 3.1: the field is swept
+ * in small steps and each step minimised from the previous minimum).  Host
+ * only, no context.  The sweep direction is u = (fields[n-1] - fields[0]) /
+ * its norm (or fields[n-1] / its norm when the two ends coincide); H_c is
+ * |mu0 H . u| where M . u first changes sign, linearly interpolated between
+ * the two bracketing steps (a step with M . u exactly 0 gives its own
+ * field).
+ *   fields [n][3] mu0*H in tesla, M [n][3] reduced magnetisation per step
+ *   (mm_stats.M); *hc_out in tesla, *found = 1, or *found = 0 (and *hc_out
+ *   untouched) when M . u never changes sign.
+ * MM_ERR_ARG for null pointers, n < 2, non-finite input or a zero sweep
+ * direction. */
+int mm_coercive_field(int64_t n, const double* fields, const double* M, double* hc_out, int32_t* found);
+
 /* Energy and gradient at m without any device allocation in the call.
  * The paper has no counterpart; this entry point is for callers that cannot
  * call cudaMalloc: a process whose device memory is handed in full to its

@@ -9,7 +9,7 @@ which M.u changes sign, u the unit vector of the sweep direction
 (fields[-1] - fields[0]), by linear interpolation between the two bracketing
 steps; it is reported as |mu0 H . u| in tesla.
 
-Pins (tests/test_oracle_curve.py): the Stoner-Wohlfarth switching field of a
+Pins (tests/test_oracle_ncg.py): the Stoner-Wohlfarth switching field of a
 small exchange-coupled particle, and the zero-crossing interpolation on
 hand-made records.
 """

@@ -107,6 +107,8 @@ EXPORTS = {
                                      C.c_double, C.c_double]),
     "mm_energy_gradient_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mm_params),
                                              C.c_void_p, C.c_int, C.c_void_p]),
+    "mm_coercive_field": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int32)]),
     "mm_stream": (C.c_void_p, [C.c_void_p]),
 }
 

@@ -232,6 +232,23 @@ class Magnet:
         return ms.value
 
 
+def coercive_field(fields, M):
+    """Coercive field (tesla) of a demagnetisation curve from the applied
+    fields [n, 3] and the reduced magnetisation per step [n, 3]
+    (mm_coercive_field); None if M never changes sign along the sweep."""
+    lib = L.load()
+    f = _f64(fields).reshape(-1, 3)
+    m = _f64(M).reshape(-1, 3)
+    if f.shape != m.shape:
+        raise ValueError("fields and M must have the same shape [n, 3]")
+    hc = C.c_double()
+    found = C.c_int32()
+    rc = lib.mm_coercive_field(len(f), _ptr(f), _ptr(m), C.byref(hc), C.byref(found))
+    if rc != 0:
+        raise MMError(rc, "mm_coercive_field rejected its arguments")
+    return hc.value if found.value else None
+
+
 def batch_plan(work, total_blocks, gamma=1.0):
     """Team sizes for a batch (pure host computation, no GPU needed)."""
     lib = L.load()

@@ -1348,6 +1348,42 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     return set_m_from_stage(ctx);
 }
 
+int mm_coercive_field(int64_t n, const double* fields, const double* M, double* hc_out, int32_t* found) {
+    if (n < 2 || !fields || !M || !hc_out || !found) return MM_ERR_ARG;
+    for (int64_t k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(fields[k]) || !std::isfinite(M[k])) return MM_ERR_ARG;
+    const double* f0 = fields;
+    const double* f1 = fields + 3 * (n - 1);
+    double u[3] = {f1[0] - f0[0], f1[1] - f0[1], f1[2] - f0[2]};
+    double nu = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (nu == 0.0) {
+        for (int c = 0; c < 3; ++c) u[c] = f1[c];
+        nu = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    }
+    if (!(nu > 0.0)) return MM_ERR_ARG;
+    for (int c = 0; c < 3; ++c) u[c] /= nu;
+    auto along = [&](const double* v, int64_t k) {
+        return v[3 * k] * u[0] + v[3 * k + 1] * u[1] + v[3 * k + 2] * u[2];
+    };
+    *found = 0;
+    for (int64_t k = 1; k < n; ++k) {
+        const double ma = along(M, k - 1), mb = along(M, k);
+        const double ha = along(fields, k - 1), hb = along(fields, k);
+        if (ma == 0.0) {
+            *hc_out = std::fabs(ha);
+            *found = 1;
+            return MM_OK;
+        }
+        if (ma * mb < 0.0) {
+            const double t = ma / (ma - mb);
+            *hc_out = std::fabs(ha + t * (hb - ha));
+            *found = 1;
+            return MM_OK;
+        }
+    }
+    return MM_OK;
+}
+
 int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi, int64_t* nnz_mag, int64_t* nnz_phi) {
     if (!ctx || !ctx->has_mesh) return MM_ERR_STATE;
     if (n_mag) *n_mag = ctx->nm;
