@@ -1,16 +1,25 @@
 """Benchmark: NCG iterations per second of the preconditioned NCG minimiser
-over the field steps of a demagnetisation curve (Sec. 3.1, Algorithm 4).
+over the field steps of a demagnetisation curve (Sec. 3.1, Algorithm 4),
+against the plain FP64 GPU method on the same field steps.
 
-Workload (default): an Nd2Fe14B cube, 80 nm edge, 48^3 voxels of 6 jittered
-tetrahedra (117,649 magnetic nodes), easy axis 1 degree off z, in an air box
-of twice the edge (97^3 lattice, 857,375 potential unknowns, 5.3M tets);
-m0 = +z; field along -z from 0 to -8 T in 40 values.  One step = one field
-step of the curve: set the field, minimise by Algorithm 4 until t1-t3 hold.
+Workload (default, large_polycrystal): a polycrystalline Nd2Fe14B cube,
+250 nm edge, 149^3 voxels of 6 tetrahedra (19.8 M magnet tets, 3,375,000
+magnetic nodes), 125 Voronoi grains with easy axes uniform in a 15 degree
+cone about +z and a 2 nm grain-boundary phase (Ms and K1 at 40%), in an air
+box of twice the edge graded by 1.06 per cell (53.2 M tets, 8,741,816
+potential unknowns); m0 = +z; field along -z from 0 to -8 T in 60 values.
+One step = one field step of the curve: set the field, minimise by
+Algorithm 4 until t1-t3 hold.
 
-value: NCG iterations / s with everything resident on the device (summed
-over ranks, max time over ranks).  e2e: the same metric through the public
-API with host buffers: each step uploads m from pinned host memory, sets the
-field, minimises and reads m and the stats back.
+value: NCG iterations / s of the precision form (FP32 potential solve
+preconditioned by the multigrid V-cycle, FP64 refinement, FP64 everything
+else) with everything resident on the device (summed over ranks, max time
+over ranks).  plain_fp64: the same field steps (a prefix of them, see
+--fp64-steps) in plain FP64 (Jacobi-preconditioned potential CG).  e2e: the
+headline form through the public API with host buffers: each step uploads m
+from pinned host memory, sets the field, minimises and reads m back.
+demag_curve: full 40-field curves of the 80 nm hard cube (117,649 magnetic
+nodes) in the precision and plain FP64 forms, wall time and coercive field.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -23,8 +32,8 @@ import sys
 import tempfile
 import time
 
-# the CPU oracle legs run on one host core: pin the BLAS / OpenMP pools
-# before numpy is imported so that the reported core count is the real one
+# the CPU oracle legs run in subprocesses with their own thread settings;
+# this process pins the BLAS / OpenMP pools to one thread before numpy loads
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -35,27 +44,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "NCG iters/s & demag-curve wall time vs plain FP64 GPU at equal energy tol"
 UNIT = "NCG it/s"
+WORKLOADS = ["large_polycrystal", "large_polycrystal_patches", "polycrystal", "hard_cube", "medium",
+             "soft_cube", "small"]
 
 
-def workload(name):
+def workload(name, sample=False):
+    """The named workload; sample=True gives the same recipe at the reduced
+    resolution the CPU oracle legs time (32 voxels per magnet edge for the
+    large polycrystal)."""
     import synth
+    if name == "large_polycrystal":
+        return synth.large_polycrystal(n_mag=32) if sample else synth.large_polycrystal()
+    if name == "large_polycrystal_patches":
+        return synth.large_polycrystal(n_mag=32 if sample else 149, patches_per_grain=10)
+    if name == "polycrystal":
+        return synth.polycrystal_cube(n_mag=32 if sample else 114)
     if name == "hard_cube":
-        return synth.hard_cube()
+        return synth.hard_cube(n_mag=24 if sample else 48)
     if name == "soft_cube":
         return synth.soft_cube()
     if name == "medium":
-        return synth.hard_cube(n_mag=44)
+        return synth.hard_cube(n_mag=24 if sample else 44)
     if name == "small":
         return synth.hard_cube(n_mag=12)
-    if name == "polycrystal":
-        return synth.polycrystal_cube()
     raise ValueError(name)
 
 
 def workload_desc(name, wl, sizes=None):
     d = {"workload": f"{wl.name}: {name}", "n_nodes": wl.mesh.n_nodes, "n_tets": wl.mesh.n_tets,
          "fields": f"{len(wl.fields)} values from {wl.fields[0].tolist()} to {wl.fields[-1].tolist()} T",
-         "precision": "plain FP64", "jmax": 4, "tau_F": 1e-10, "poisson_tol": 1e-10,
+         "jmax": 4, "tau_F": 1e-10, "poisson_tol": 1e-10,
          "l2": "working set larger than L2 (no flush needed)"}
     if sizes:
         d.update(sizes)
@@ -63,16 +81,17 @@ def workload_desc(name, wl, sizes=None):
 
 
 # ------------------------------------------------------------ algorithmic bytes
-def form_params(form):
+def form_params(form, theta_max=0.1):
     """Parameters of the three forms of a field step: 0 plain FP64
     (Jacobi-preconditioned potential solve), 1 precision form with Jacobi,
     2 precision form with the multigrid preconditioner (the headline)."""
     from paper_1801_03690_gb300 import Params
     if form == 0:
-        return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=0)
+        return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=0, theta_max=theta_max)
     if form == 1:
-        return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1)
-    return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1, amg=1, inner_tol=1e-3)
+        return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1, theta_max=theta_max)
+    return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1, amg=1, inner_tol=1e-3,
+                  theta_max=theta_max)
 
 
 def vcycle_bytes(amg):
@@ -108,6 +127,8 @@ def alg_bytes(st, sz, amg=None):
       trial point (evals-1) 112 n_mag
       inner step (li)       12 nnz_mag + 352 n_mag  (H product + update)
       per iteration (nli+1) 272 n_mag               (inner set-up + direction)
+    nnz_phi is the stored potential stiffness (without the rounding residues
+    the upload drops).
     """
     nphi, nm = sz["n_phi"], sz["n_mag"]
     nzp, nzm = sz["nnz_phi"], sz["nnz_mag"]
@@ -179,10 +200,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def merge_clocks(cks):
+    cks = [c for c in cks if c]
+    if not cks:
+        return None
+    return {"sm_mhz": statistics.median([c["sm_mhz"] for c in cks]), "sm_max_mhz": max(c["sm_max_mhz"] for c in cks),
+            "reasons": sorted(set().union(*[set(c["reasons"]) for c in cks])),
+            "samples": sum(c["samples"] for c in cks)}
+
+
 # ------------------------------------------------------------------ traffic
 KERNEL_SOURCES = ["paper_1801_03690_gb300/csrc/mm_solver_body.cuh",
                   "paper_1801_03690_gb300/csrc/mm_internal.cuh"]
-PROFILE = "profiles/k_solver_hard_cube.md"
+TRAFFIC = "profiles/k_solver_traffic.json"
 
 
 def kernel_source_digest():
@@ -193,18 +223,18 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
-def traffic_ratio():
-    """DRAM bytes / algorithmic bytes of the solver kernel from the last ncu
-    capture summarised in profiles/ (a line 'traffic_ratio: R sources: D'),
-    or None when the kernel sources changed since that capture."""
+def traffic_record(workload_name):
+    """The ncu DRAM-traffic record of the solver kernel on this workload
+    (profiles/k_solver_traffic.json, written from one capture of
+    dram__bytes_read.sum + dram__bytes_write.sum), or None when there is
+    none for this workload or the kernel sources changed since."""
     try:
-        for line in open(os.path.join(ROOT, PROFILE)):
-            if line.startswith("traffic_ratio:"):
-                f = line.split()
-                if f[3] == kernel_source_digest():
-                    return float(f[1])
-    except (OSError, IndexError, ValueError):
-        pass
+        recs = json.load(open(os.path.join(ROOT, TRAFFIC)))
+    except (OSError, ValueError):
+        return None
+    for r in recs.get("records", []):
+        if r.get("workload") == workload_name and r.get("sources") == kernel_source_digest():
+            return r
     return None
 
 
@@ -242,25 +272,73 @@ class Ranks:
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(wl, max_iter, warm_iter=0):
-    """The CPU oracle as it stands: assemble, then Algorithm 4 at the first
-    field from m0 with the potential solved by Algorithm 1 (the same
-    algorithm as the GPU).  Returns (nli, seconds, description)."""
+def oracle_sample(name, first_field, n_iter):
+    """The CPU oracle as it stands, on the reduced-resolution sample of the
+    workload's recipe (workload(name, sample=True)): assembly, then
+    Algorithm 4 with the potential solved by Algorithm 1 (the same algorithm
+    as the GPU's plain FP64 form) from m0 at field index first_field, for
+    exactly n_iter NCG iterations, continuing into the next field indices
+    whenever a field converges first.  Returns a dict with the timed
+    seconds (assembly excluded), the counters and the sample's sizes."""
     from oracle import fem, energy, ncg
-    P = fem.assemble_workload(wl)
-    m = energy.normalize(wl.m0[P.mag_nodes])
-    h = P.units.field_int(wl.fields[0])
-    phi = None
-    if warm_iter:
-        r = ncg.minimize(P, m, h, ncg.Params(jmax=4, poisson="cg", max_iter=warm_iter))
-        m, phi = r.m, r.phi
+    wl = workload(name, sample=True)
     t0 = time.perf_counter()
-    r = ncg.minimize(P, m, h, ncg.Params(jmax=4, poisson="cg", max_iter=max_iter), phi0=phi)
+    P = fem.assemble_workload(wl)
+    t_asm = time.perf_counter() - t0
+    m = energy.normalize(wl.m0[P.mag_nodes])
+    phi = None
+    tot = {"nli": 0, "evals": 0, "mi": 0, "li": 0, "ls_extra": 0}
+    fields = []
+    k = first_field
+    t0 = time.perf_counter()
+    while tot["nli"] < n_iter and k < len(wl.fields):
+        r = ncg.minimize(P, m, P.units.field_int(wl.fields[k]),
+                         ncg.Params(jmax=4, poisson="cg", max_iter=n_iter - tot["nli"]), phi0=phi)
+        m, phi = r.m, r.phi
+        for c in tot:
+            tot[c] += r.stats[c]
+        fields.append(k)
+        k += 1
     dt = time.perf_counter() - t0
-    desc = (f"oracle Algorithm 4 at the first field of the same workload, {r.stats['nli']} NCG "
-            f"iteration(s) incl. the initial evaluation ({r.stats['evals']} evaluations, "
-            f"{r.stats['mi']} potential steps), assembly excluded")
-    return r.stats["nli"], dt, desc
+    return {"seconds": dt, "assembly_s": t_asm, **tot, "fields": fields, "sample": wl.name,
+            "n_phi": P.n_phi, "n_mag": P.n_mag}
+
+
+def oracle_leg(name, first_field, n_iter, threads):
+    """oracle_sample in a child process whose BLAS / OpenMP pools have
+    `threads` threads (numpy reads the setting at import)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", "--workload", name,
+                        "--oracle-first-field", str(first_field), "--oracle-iters", str(n_iter)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle leg failed:\n" + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["threads"] = threads
+    return out
+
+
+def oracle_baseline_entry(o, full=None):
+    """cpu_baseline object of one oracle leg; with full = (n_phi, potential
+    steps per NCG iteration of the GPU's plain FP64 form at full size), an
+    estimate of the oracle at full size scaled by unknowns x potential steps
+    per iteration (labelled extrapolated)."""
+    v = o["nli"] / o["seconds"]
+    e = {"value": v, "unit": UNIT, "cores": o["threads"], "kind": "oracle",
+         "sample": (f"oracle Algorithm 4 (Jacobi-CG potential solve) on {o['sample']} (the same recipe at reduced "
+                    f"resolution: {o['n_phi']} potential unknowns, {o['n_mag']} magnetic nodes) from m0 at field "
+                    f"indices {o['fields']}, {o['nli']} NCG iterations, {o['evals']} evaluations, {o['mi']} "
+                    f"potential steps, {o['seconds']:.1f} s; assembly ({o['assembly_s']:.1f} s) excluded")}
+    if full and o["nli"] and o["mi"]:
+        n_phi_full, mi_per_it_full = full
+        scale = (n_phi_full / o["n_phi"]) * (mi_per_it_full / (o["mi"] / o["nli"]))
+        e["extrapolated_full_size"] = {"value": v / scale, "unit": UNIT,
+                                       "how": "sample time per iteration x (full/sample unknowns) x (full/sample "
+                                              "potential steps per iteration; full = the GPU plain FP64 form's "
+                                              "counts on the same fields): extrapolated, not measured"}
+    return e
 
 
 # ------------------------------------------------------------------ main
@@ -270,9 +348,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hard_cube", choices=["hard_cube", "medium", "soft_cube", "small", "polycrystal"])
+    ap.add_argument("--workload", default="large_polycrystal", choices=WORKLOADS)
+    ap.add_argument("--fp64-steps", type=int, default=8,
+                    help="timed field steps of the plain FP64 comparison (a prefix of the timed steps)")
+    ap.add_argument("--jacobi", action="store_true", help="also time the Jacobi-preconditioned precision form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-curve", action="store_true", help="skip the full hard-cube curves")
     ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling"],
                     help="steps: the timed field steps (default line); curve: full demagnetisation "
                          "curves of the plain FP64, precision and precision + learned forms; "
@@ -286,24 +368,37 @@ def main():
                     help="warm start: cap on the largest predicted nodal change")
     ap.add_argument("--blocks-per-sm", type=int, default=0,
                     help="solver kernel instantiation / grid (0 = default)")
+    ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-first-field", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-iters", type=int, default=5, help=argparse.SUPPRESS)
     args = ap.parse_args()
     K, W = args.steps, max(args.warmup, 0)
+
+    if args.oracle_leg:
+        print(json.dumps(oracle_sample(args.workload, args.oracle_first_field, args.oracle_iters)))
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
+        # the oracle (no reference implementation exists: the reference is
+        # the paper's text), timed on the host cores for exactly K NCG
+        # iterations; one step = one NCG iteration (the metric's unit)
         if rank != 0:
             return 0
-        wl = workload(args.workload)
-        nli, dt, desc = oracle_sample(wl, max_iter=K, warm_iter=W)
-        v = nli / dt
+        cores = os.cpu_count() or 1
+        o = oracle_leg(args.workload, W, K, cores)
+        v = o["nli"] / o["seconds"]
+        cb = oracle_baseline_entry(o)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": K, "warmup": W, "ms_per_step": 1000.0 * dt / max(nli, 1),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": workload_desc(args.workload, wl),
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+                "steps": o["nli"], "warmup": 0, "ms_per_step": 1000.0 * o["seconds"] / max(o["nli"], 1),
+                "step": "one NCG iteration of the oracle", "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(workload_desc(args.workload, workload(args.workload, sample=True)),
+                               sample_of=args.workload),
+                "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
@@ -313,7 +408,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local_rank)
-    from paper_1801_03690_gb300 import Magnet, Params
+    from paper_1801_03690_gb300 import Magnet, coercive_field
 
     if args.mode == "curve":
         return curve_mode(args, rank, local_rank)
@@ -322,27 +417,37 @@ def main():
     if args.mode == "scaling":
         return scaling_mode(args, rank, local_rank)
 
+    t0 = time.perf_counter()
     wl = workload(args.workload)
+    t_gen = time.perf_counter() - t0
     fields = wl.fields
-    if W + K > len(fields):
-        raise SystemExit(f"--warmup + --steps must be <= {len(fields)} field steps")
+    if W < 1 or W + K > len(fields):
+        raise SystemExit(f"need --warmup >= 1 and --warmup + --steps <= {len(fields)} field steps")
     mag = Magnet(device=local_rank, blocks_per_sm=args.blocks_per_sm)
+    t0 = time.perf_counter()
     mag.upload_workload(wl)
+    t_up = time.perf_counter() - t0
     sz = mag.sizes()
     stream = torch.cuda.ExternalStream(mag.stream, device=torch.device("cuda", local_rank))
-
     ranks = Ranks(world, torch.device("cuda", local_rank))
     barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
-
     amg = mag.amg_info()
 
-    def run_form(prm):
-        """W untimed field steps from m0, then K timed field steps."""
+    # warm-up: W field steps from m0 in the headline form; every timed form
+    # then starts from this state, re-converging the last warm-up field in
+    # its own form (untimed) so that its potential is its own
+    head = form_params(2)
+    mag.set_magnetization(wl.m0)
+    for k in range(W):
+        mag.set_field(fields[k])
+        mag.minimize(head)
+    m_w = mag.get_magnetization()
+
+    def run_form(prm, n):
         lv = amg if prm.amg else None
-        mag.set_magnetization(wl.m0)
-        for k in range(W):
-            mag.set_field(fields[k])
-            mag.minimize(prm)
+        mag.set_magnetization(m_w)
+        mag.set_field(fields[W - 1])
+        mag.minimize(prm)
         clocks = ClockSampler(local_rank)
         barrier()
         torch.cuda.synchronize()
@@ -351,42 +456,43 @@ def main():
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         nli, kern_ms, nbytes, per_step = 0, 0.0, 0, []
-        for k in range(W, W + K):
+        for k in range(W, W + n):
             mag.set_field(fields[k])
             mag.minimize_async(prm)
             st = mag.get_stats()
             ms = mag.last_kernel_ms()
+            b = alg_bytes(st, sz, lv)
             kern_ms += ms
-            nbytes += alg_bytes(st, sz, lv)
+            nbytes += b
             nli += st["nli"]
             per_step.append({"field_T": float(fields[k][2]), "status": st["status"], "nli": st["nli"],
                              "evals": st["evals"], "mi": st["mi"], "mr": st["mr"], "li": st["li"],
-                             "F_J": st["F"], "Mz": st["M"][2], "kernel_ms": ms})
+                             "ls_extra": st["ls_extra"], "F_J": st["F"], "Mz": st["M"][2], "kernel_ms": ms,
+                             "alg_GB": b / 1e9})
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
         ck = clocks.stop()
         t_ms = max_over_ranks(ev0.elapsed_time(ev1))
         nli_all = sum_over_ranks(nli)
-        return {"prm": prm, "value": nli_all / (t_ms / 1000.0), "t_ms": t_ms, "nli": nli_all,
+        return {"prm": prm, "value": nli_all / (t_ms / 1000.0), "t_ms": t_ms, "nli": nli_all, "n": n,
                 "kern_ms": kern_ms, "bytes": nbytes, "per_step": per_step, "clocks": ck,
                 "m": mag.get_magnetization(), "F": per_step[-1]["F_J"]}
 
-    fp64 = run_form(form_params(0))
-    jac = run_form(form_params(1))
-    x1 = run_form(form_params(2))
+    x1 = run_form(head, K)
+    n64 = max(1, min(K, args.fp64_steps))
+    fp64 = run_form(form_params(0), n64)
+    jac = run_form(form_params(1), n64) if args.jacobi else None
 
-    # ---- end to end through the public API with host buffers (precision form)
+    # ---- end to end through the public API with host buffers (headline form)
     e2e = None
     if not args.no_e2e:
-        prm = x1["prm"]
+        prm = head
         m_host = torch.empty((wl.mesh.n_nodes, 3), dtype=torch.float64).pin_memory()
-        m_host.copy_(torch.from_numpy(wl.m0))
+        m_host.copy_(torch.from_numpy(m_w))
         mag.set_magnetization(m_host.numpy())
-        for k in range(W):
-            mag.set_field(fields[k])
-            mag.minimize(prm)
-        m_host.copy_(torch.from_numpy(mag.get_magnetization()))
+        mag.set_field(fields[W - 1])
+        mag.minimize(prm)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -402,7 +508,37 @@ def main():
         te = max_over_ranks(time.perf_counter() - t0)
         mbytes = wl.mesh.n_nodes * 3 * 8
         e2e = {"value": sum_over_ranks(nli_e) / te, "unit": UNIT, "h2d_bytes_per_step": mbytes + 24,
-               "d2h_bytes_per_step": mbytes + 144, "form": "precision form (FP32 potential solve + FP64 refinement)"}
+               "d2h_bytes_per_step": mbytes + 144, "form": "headline form (multigrid precision form)"}
+    mag.close()
+
+    # ---- full demagnetisation curves of the 80 nm hard cube in both forms
+    curves = None
+    if not args.no_curve:
+        import synth
+        hc_wl = synth.hard_cube()
+        cm = Magnet(device=local_rank, blocks_per_sm=args.blocks_per_sm)
+        cm.upload_workload(hc_wl)
+        curves = {"workload": f"{hc_wl.name}: 80 nm Nd2Fe14B cube, {len(hc_wl.fields)} fields 0 to -8 T",
+                  "sizes": cm.sizes()}
+        for name, prm in (("precision_multigrid", form_params(2)), ("plain_fp64", form_params(0))):
+            cm.set_magnetization(hc_wl.m0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sts = cm.demag_curve(hc_wl.fields, prm)
+            torch.cuda.synchronize()
+            wall = max_over_ranks(time.perf_counter() - t0)
+            M = np.array([s["M"] for s in sts])
+            curves[name] = {"wall_s": wall, "nli": int(sum(s["nli"] for s in sts)),
+                            "evals": int(sum(s["evals"] for s in sts)), "mi": int(sum(s["mi"] for s in sts)),
+                            "Hc_T": coercive_field(hc_wl.fields, M),
+                            "statuses": sorted(set(s["status"] for s in sts)), "M": M[:, 2].tolist()}
+        a, b = curves["precision_multigrid"], curves["plain_fp64"]
+        curves["speedup_vs_plain_fp64"] = b["wall_s"] / a["wall_s"]
+        curves["Hc_rel_diff"] = (abs(a["Hc_T"] - b["Hc_T"]) / b["Hc_T"]) if a["Hc_T"] and b["Hc_T"] else None
+        curves["max_abs_dMz"] = float(np.max(np.abs(np.array(a["M"]) - np.array(b["M"]))))
+        for f in ("precision_multigrid", "plain_fp64"):
+            curves[f].pop("M")
+        cm.close()
 
     if rank != 0:
         return 0
@@ -412,55 +548,64 @@ def main():
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)" if hbm else "fallback"
     hbm = hbm or 6800.0
     achieved = x1["bytes"] / (x1["kern_ms"] / 1000.0) / 1e9
-    ratio = traffic_ratio()
     ach64 = fp64["bytes"] / (fp64["kern_ms"] / 1000.0) / 1e9
-    achj = jac["bytes"] / (jac["kern_ms"] / 1000.0) / 1e9
-    dm = float(np.abs(x1["m"] - fp64["m"]).max())
+    tr = traffic_record(args.workload)
+    # the headline form on exactly the fields of the FP64 comparison
+    x1_sub_ms = sum(p["kernel_ms"] for p in x1["per_step"][:n64])
+    x1_sub_nli = sum(p["nli"] for p in x1["per_step"][:n64])
+    fp64_ms = sum(p["kernel_ms"] for p in fp64["per_step"])
     line = {
         "metric": METRIC, "value": x1["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": x1["t_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp32+fp64", "data": "synthetic",
+        "dtype": "fp32+fp64", "data": "synthetic (seeded generators in synth/)",
         "config": workload_desc(args.workload, wl, sz),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
-                     "traffic": (ratio * x1["bytes"] / K) if ratio else None, "kernel": "k_solver",
-                     "peak_source": peak_src, "alg_bytes_per_launch": x1["bytes"] / K,
-                     "kernel_ms_per_launch": x1["kern_ms"] / K},
-        "plain_fp64": {"value": fp64["value"], "unit": UNIT, "ms_per_step": fp64["t_ms"] / K,
-                       "dtype": "f64", "roofline_frac": ach64 / hbm, "achieved_gbs": ach64,
+                     "traffic": (tr["ratio"] * x1["bytes"] / K) if tr else None,
+                     "traffic_source": (f"{TRAFFIC}: DRAM bytes / algorithmic bytes = {tr['ratio']:.3f} from one "
+                                        f"ncu capture ({tr['note']})") if tr else None,
+                     "kernel": "k_solver", "peak_source": peak_src,
+                     "alg_bytes_per_launch": x1["bytes"] / K, "kernel_ms_per_launch": x1["kern_ms"] / K},
+        "plain_fp64": {"value": fp64["value"], "unit": UNIT, "ms_per_step": fp64["t_ms"] / n64,
+                       "fields_timed": n64, "dtype": "f64", "roofline_frac": ach64 / hbm, "achieved_gbs": ach64,
                        "per_step": fp64["per_step"]},
-        "precision_jacobi": {"value": jac["value"], "unit": UNIT, "ms_per_step": jac["t_ms"] / K,
-                             "dtype": "fp32+fp64", "roofline_frac": achj / hbm, "achieved_gbs": achj,
-                             "per_step": jac["per_step"]},
+        "vs_plain_fp64_same_fields": {
+            "fields": [W, W + n64 - 1],
+            "headline_nli_per_s": x1_sub_nli / (x1_sub_ms / 1000.0),
+            "plain_fp64_nli_per_s": fp64["nli"] / (fp64_ms / 1000.0),
+            "kernel_time_ratio": fp64_ms / x1_sub_ms,
+            "final_energy_rel_diff": abs(x1["per_step"][n64 - 1]["F_J"] - fp64["F"]) / abs(fp64["F"]),
+            "final_Mz_abs_diff": abs(x1["per_step"][n64 - 1]["Mz"] - fp64["per_step"][-1]["Mz"])},
         "multigrid": {"levels": amg, "inner_tol": x1["prm"].inner_tol},
-        "demag_curve": {"fields_timed": K, "wall_s_precision_form": x1["t_ms"] / 1000.0,
-                        "wall_s_plain_fp64": fp64["t_ms"] / 1000.0,
-                        "wall_s_precision_jacobi": jac["t_ms"] / 1000.0,
-                        "speedup_vs_plain_fp64": fp64["t_ms"] / x1["t_ms"],
-                        "speedup_vs_precision_jacobi": jac["t_ms"] / x1["t_ms"],
-                        "final_energy_rel_diff": abs(x1["F"] - fp64["F"]) / abs(fp64["F"]),
-                        "final_max_abs_dm": dm, "per_step": x1["per_step"]},
+        "timed_fields": {"fields": [W, W + K - 1], "wall_s": x1["t_ms"] / 1000.0, "per_step": x1["per_step"]},
+        "setup_s": {"generate": t_gen, "upload_and_assembly": t_up},
         "gpu_launches": 2 * K,
+        "gpu_launches_note": "per timed field step: k_set_field and one persistent k_solver launch",
     }
-    line["config"]["precision"] = ("precision form: FP32 potential solve preconditioned by the multigrid V-cycle "
-                                   "+ FP64 refinement (Jacobi-preconditioned in precision_jacobi, plain FP64 "
-                                   "in plain_fp64)")
+    line["config"]["precision"] = ("headline: FP32 potential solve preconditioned by the multigrid V-cycle + FP64 "
+                                   "refinement, FP64 energy/gradient/line search/NCG; plain_fp64: FP64 throughout, "
+                                   "Jacobi-preconditioned potential CG")
+    if jac:
+        achj = jac["bytes"] / (jac["kern_ms"] / 1000.0) / 1e9
+        line["precision_jacobi"] = {"value": jac["value"], "unit": UNIT, "ms_per_step": jac["t_ms"] / n64,
+                                    "fields_timed": n64, "roofline_frac": achj / hbm, "per_step": jac["per_step"]}
+    if curves:
+        line["demag_curve"] = curves
     if e2e:
         line["e2e"] = e2e
-    if x1["clocks"]:
-        line["clocks"] = x1["clocks"]
-        for o in (fp64, jac):
-            if o["clocks"]:
-                line["clocks"]["reasons"] = sorted(set(line["clocks"]["reasons"]) | set(o["clocks"]["reasons"]))
+    ck = merge_clocks([x1["clocks"], fp64["clocks"], jac["clocks"] if jac else None])
+    if ck:
+        line["clocks"] = ck
     if world == 1 and not args.no_cpu_baseline:
-        nli_c, dt_c, desc = oracle_sample(wl, max_iter=1)
-        line["cpu_baseline"] = {"value": nli_c / dt_c, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": desc}
+        full = (sz["n_phi"], sum(p["mi"] for p in fp64["per_step"]) / max(1, fp64["nli"]))
+        legs = [oracle_leg(args.workload, W, 5, 1), oracle_leg(args.workload, W, 5, os.cpu_count() or 1)]
+        best = max(legs, key=lambda o: o["nli"] / o["seconds"])
+        line["cpu_baseline"] = oracle_baseline_entry(best, full)
+        line["cpu_baseline"]["legs"] = [oracle_baseline_entry(o, full) for o in legs]
     print(json.dumps(line))
-    mag.close()
     return 0
 
 
@@ -471,8 +616,7 @@ def curve_mode(args, rank, local_rank):
     start (network trained on the curve of a coarser mesh of the same
     recipe).  Reports wall time, NCG iterations and coercive field."""
     import torch
-    from paper_1801_03690_gb300 import Magnet, Params, MLP, warmstart
-    from paper_1801_03690_gb300.curves import coercive_field
+    from paper_1801_03690_gb300 import Magnet, Params, MLP, warmstart, coercive_field
     wl = workload(args.workload)
     fields = wl.fields
     mag = Magnet(device=local_rank, blocks_per_sm=args.blocks_per_sm)

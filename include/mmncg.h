@@ -112,6 +112,11 @@ typedef struct {
     double terms[4];       /* exchange, anisotropy, magnetostatic, Zeeman; J      */
     double F_internal;     /* energy in internal units (what t1-t3 see)           */
     double M[3];           /* sum_i w_i m_i / sum_i w_i (reduced magnetisation)   */
+    /* branches taken (Sec. 3.1 li2, the descent safeguard of Alg. 4):        */
+    int64_t li2;           /* preconditioner solves ended by negative curvature   */
+    int64_t li2_first;     /* ... of them on the first inner step (y = g)         */
+    int64_t restarts;      /* new directions whose y was replaced by g (g.d >= 0) */
+    int64_t steepest;      /* directions that fell back to d = -g                 */
 } mm_stats;
 
 void mm_default_params(mm_params* p);
@@ -225,6 +230,21 @@ int mm_hessian_apply(mm_ctx* ctx, const mm_params* p, const double* v,
  * out = K_phi v on the unknowns, with v and out [n_nodes] host arrays
  * (entries on the outer surface are ignored / written as 0). */
 int mm_potential_matvec(mm_ctx* ctx, const double* v, double* out);
+
+/* One product with an operator of Eq. (energy) (Sec. 2.2, 3.1), the same
+ * device code the minimiser applies, in internal units (lengths in nm,
+ * magnetisation in units of Mref; v and out are host arrays indexed by node):
+ *   MM_OP_DIV    out[n_nodes]    = D v: the right-hand side of the potential
+ *                equation K_phi phi = D m for v = m ([n_nodes][3], used as
+ *                given, not normalised); 0 off the potential unknowns
+ *   MM_OP_DIVT   out[n_nodes][3] = D^T v for a potential v [n_nodes] (entries
+ *                on the outer surface ignored): the magnetostatic part of
+ *                grad F; 0 on non-magnetic nodes
+ *   MM_OP_LOCAL  out[n_nodes][3] = (C_A + C_K) v for v [n_nodes][3]: the
+ *                exchange and anisotropy part of grad F
+ * MM_ERR_ARG for an unknown op or null arrays. */
+enum { MM_OP_DIV = 0, MM_OP_DIVT = 1, MM_OP_LOCAL = 2 };
+int mm_operator_apply(mm_ctx* ctx, int32_t op, const double* v, double* out);
 
 /* Demagnetisation curve (Sec. 3.1): for each of n_fields applied fields
  * mu0*H (tesla, [n_fields][3]) set the field and minimise from the previous

@@ -37,7 +37,9 @@ path):
   * Counters: evals (function evaluations), nli (iterations), li (products
     with H in the inner solves), mi (products with K_phi in the loop of the
     Poisson solves; 0 with the direct solver), ls_extra (evaluations spent
-    backtracking).
+    backtracking); the branches taken: li2 (inner solves ended by negative
+    curvature), li2_first (of them on the first step: y = g), restarts (y
+    replaced by g in the safeguard), steepest (d = -g).
 
 Pins (tests/test_oracle_ncg.py): the Stoner-Wohlfarth switching field of a
 small particle (exchange-coupled uniform rotation, demag off), the exact
@@ -88,14 +90,21 @@ def beta_za(g_new, g_old, y_new, d_old):
     return 0.0
 
 
-def direction(g_new, g_old, y_new, d_old):
-    """d = -y + beta*ZA d_old with the descent safeguard."""
+def direction(g_new, g_old, y_new, d_old, counts=None):
+    """d = -y + beta*ZA d_old with the descent safeguard.  With a dict
+    `counts`, the safeguard's branches are tallied: counts["restarts"] when
+    y is replaced by g, counts["steepest"] when d falls back to -g
+    (bookkeeping only)."""
     beta = beta_za(g_new, g_old, y_new, d_old)
     d = -y_new + beta * d_old
     if float(np.sum(g_new * d)) >= 0.0:
+        if counts is not None:
+            counts["restarts"] = counts.get("restarts", 0) + 1
         beta = beta_za(g_new, g_old, g_new, d_old)
         d = -g_new + beta * d_old
         if float(np.sum(g_new * d)) >= 0.0:
+            if counts is not None:
+                counts["steepest"] = counts.get("steepest", 0) + 1
             d = -g_new.copy()
     return d
 
@@ -117,7 +126,8 @@ def cubic_step(f0, g0, a, f1, g1):
 def minimize(P, m0, h, params=None, phi0=None):
     """Minimise F at reduced field h starting from m0 (Nm, 3)."""
     p = params or Params()
-    st = {"evals": 0, "nli": 0, "li": 0, "mi": 0, "ls_extra": 0}
+    st = {"evals": 0, "nli": 0, "li": 0, "mi": 0, "ls_extra": 0,
+          "li2": 0, "li2_first": 0, "restarts": 0, "steepest": 0}
 
     def ev(m, phi_warm):
         e = evaluate(P, m, h, p.poisson, phi0=phi_warm, tol=p.poisson_tol)
@@ -126,7 +136,7 @@ def minimize(P, m0, h, params=None, phi0=None):
         return e
 
     def pre(m, e):
-        y, steps = precond_solve(P, m, e["grad"], e["g"], p.jmax, p.keep_last_term)
+        y, steps = precond_solve(P, m, e["grad"], e["g"], p.jmax, p.keep_last_term, counts=st)
         st["li"] += steps
         return y
 
@@ -136,6 +146,7 @@ def minimize(P, m0, h, params=None, phi0=None):
     y = pre(x, e)
     d = -y
     if float(np.sum(e["g"] * d)) >= 0.0:
+        st["steepest"] += 1
         d = -e["g"].copy()
     a_prev = 1.0
     status = "max_iter"
@@ -188,7 +199,7 @@ def minimize(P, m0, h, params=None, phi0=None):
         t2 = np.max(np.abs(x - x_b)) < np.sqrt(p.tau_F) * (1.0 + np.max(np.abs(x_b)))
         t3 = np.max(np.abs(e_b["g"])) < p.tau_F ** (1.0 / 3.0) * (1.0 + abs(e_b["F"]))
         y_new = pre(x_b, e_b)
-        d = direction(e_b["g"], e["g"], y_new, d)
+        d = direction(e_b["g"], e["g"], y_new, d, counts=st)
         x, e, a_prev = x_b, e_b, a_b
         if t1 and t2 and t3:
             status = "converged"

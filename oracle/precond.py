@@ -49,8 +49,11 @@ def jacobi_diag(P):
     return d
 
 
-def precond_solve(P, m, grad, g, jmax, keep_last=False):
-    """Solve H(m) y = g approximately.  Returns (y, steps)."""
+def precond_solve(P, m, grad, g, jmax, keep_last=False, counts=None):
+    """Solve H(m) y = g approximately.  Returns (y, steps).  With a dict
+    `counts`, the exits by negative curvature (li2) are tallied in
+    counts["li2"] and, of them, those on the first step in
+    counts["li2_first"] (bookkeeping only)."""
     if jmax <= 0:
         return g.copy(), 0
     nm = m.shape[0]
@@ -68,6 +71,10 @@ def precond_solve(P, m, grad, g, jmax, keep_last=False):
     # Algorithm 1 solves C x = -b_alg1 with C = H, b_alg1 = -g, x0 = 0
     y, steps, reason = alg1(H, -rhs, np.zeros_like(rhs), Pinv, eps, jmax,
                             neg_curvature=True)
+    if counts is not None and reason == "neg_curvature":
+        counts["li2"] = counts.get("li2", 0) + 1
+        if steps == 1:
+            counts["li2_first"] = counts.get("li2_first", 0) + 1
     if reason == "neg_curvature" and steps == 1:
         y = rhs.copy()
     return y.reshape(nm, 3), steps

@@ -17,6 +17,10 @@ MM_ERR_NONFINITE = -5
 MM_ERR_DEVICE_TIMEOUT = -6
 MM_ERR_STATE = -7
 
+MM_OP_DIV = 0
+MM_OP_DIVT = 1
+MM_OP_LOCAL = 2
+
 STATUS_NAMES = {0: "ok", 1: "not_converged", 2: "stalled", -1: "err_arg", -2: "err_mesh",
                 -3: "err_oom", -4: "err_cuda", -5: "err_nonfinite", -6: "err_device_timeout",
                 -7: "err_state"}
@@ -42,7 +46,8 @@ class mm_stats(C.Structure):
     _fields_ = [("evals", C.c_int64), ("nli", C.c_int64), ("li", C.c_int64), ("mi", C.c_int64),
                 ("ls_extra", C.c_int64), ("mr", C.c_int64), ("status", C.c_int32), ("pad", C.c_int32),
                 ("F", C.c_double), ("terms", C.c_double * 4), ("F_internal", C.c_double),
-                ("M", C.c_double * 3)]
+                ("M", C.c_double * 3), ("li2", C.c_int64), ("li2_first", C.c_int64),
+                ("restarts", C.c_int64), ("steepest", C.c_int64)]
 
 
 EXPORTS = {
@@ -107,6 +112,7 @@ EXPORTS = {
                                      C.c_double, C.c_double]),
     "mm_energy_gradient_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mm_params),
                                              C.c_void_p, C.c_int, C.c_void_p]),
+    "mm_operator_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "mm_coercive_field": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int32)]),
     "mm_stream": (C.c_void_p, [C.c_void_p]),

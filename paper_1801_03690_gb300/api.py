@@ -47,7 +47,8 @@ class Params:
 def _stats_dict(s):
     return {"evals": s.evals, "nli": s.nli, "li": s.li, "mi": s.mi, "ls_extra": s.ls_extra, "mr": s.mr,
             "status": L.STATUS_NAMES.get(s.status, s.status), "status_code": s.status,
-            "F": s.F, "terms": list(s.terms), "F_internal": s.F_internal, "M": list(s.M)}
+            "F": s.F, "terms": list(s.terms), "F_internal": s.F_internal, "M": list(s.M),
+            "li2": s.li2, "li2_first": s.li2_first, "restarts": s.restarts, "steepest": s.steepest}
 
 
 def _f64(a, shape=None):
@@ -216,6 +217,27 @@ class Magnet:
         v = _f64(v, (self.n_nodes,))
         out = np.zeros(self.n_nodes)
         self._check(self._lib.mm_potential_matvec(self._h, _ptr(v), _ptr(out)))
+        return out
+
+    def divergence(self, v):
+        """D v (mm_operator_apply MM_OP_DIV): v [n_nodes, 3] -> [n_nodes]."""
+        v = _f64(v, (self.n_nodes, 3))
+        out = np.zeros(self.n_nodes)
+        self._check(self._lib.mm_operator_apply(self._h, L.MM_OP_DIV, _ptr(v), _ptr(out)))
+        return out
+
+    def divergence_t(self, phi):
+        """D^T phi (MM_OP_DIVT): phi [n_nodes] -> [n_nodes, 3]."""
+        v = _f64(phi, (self.n_nodes,))
+        out = np.zeros((self.n_nodes, 3))
+        self._check(self._lib.mm_operator_apply(self._h, L.MM_OP_DIVT, _ptr(v), _ptr(out)))
+        return out
+
+    def local_apply(self, v):
+        """(C_A + C_K) v (MM_OP_LOCAL): [n_nodes, 3] -> [n_nodes, 3]."""
+        v = _f64(v, (self.n_nodes, 3))
+        out = np.zeros((self.n_nodes, 3))
+        self._check(self._lib.mm_operator_apply(self._h, L.MM_OP_LOCAL, _ptr(v), _ptr(out)))
         return out
 
     def demag_curve(self, fields, params=None):

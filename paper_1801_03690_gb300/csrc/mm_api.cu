@@ -755,6 +755,10 @@ void fill_stats(mm_ctx* ctx, mm_stats* out) {
     for (int k = 0; k < 4; ++k) out->terms[k] = s.terms[k] * EJ;
     out->F_internal = s.F;
     for (int k = 0; k < 3; ++k) out->M[k] = s.M[k];
+    out->li2 = s.li2;
+    out->li2_first = s.li2_first;
+    out->restarts = s.restarts;
+    out->steepest = s.steepest;
 }
 
 int status_code(int st) {
@@ -1592,6 +1596,34 @@ int mm_potential_matvec(mm_ctx* ctx, const double* v, double* out) {
     CK_CUDA(cudaGetLastError());
     CK_CUDA(cudaMemcpyAsync(out, ctx->d_stage, (size_t)ctx->n_nodes * sizeof(double), cudaMemcpyDeviceToHost,
                             ctx->stream));
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int mm_operator_apply(mm_ctx* ctx, int32_t op, const double* v, double* out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (!v || !out) return fail(ctx, MM_ERR_ARG, "null array");
+    if (op != MM_OP_DIV && op != MM_OP_DIVT && op != MM_OP_LOCAL) return fail(ctx, MM_ERR_ARG, "unknown operator %d", op);
+    const size_t N = (size_t)ctx->n_nodes;
+    if (op == MM_OP_DIVT) {
+        CK_CUDA(cudaMemcpy(ctx->d_stage, v, N * sizeof(double), cudaMemcpyHostToDevice));
+        k_gather1<<<nblk(ctx->nphi), 256, 0, ctx->stream>>>(ctx->nphi, ctx->d_node_of_phi, ctx->d_ident,
+                                                             ctx->d_stage, ctx->P.pdir[0]);
+    } else {
+        CK_CUDA(cudaMemcpy(ctx->d_stage, v, 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+        k_gather3<<<nblk(ctx->nm), 256, 0, ctx->stream>>>(ctx->nm, ctx->d_mag_nodes, ctx->d_stage, ctx->P.idir[0]);
+    }
+    CK_CUDA(cudaGetLastError());
+    const int mode = (op == MM_OP_DIV) ? mm::MODE_DIV : (op == MM_OP_DIVT) ? mm::MODE_DIVT : mm::MODE_LOCAL;
+    if ((rc = launch_solver(ctx, mode, to_params(nullptr)))) return rc;
+    if ((rc = finish(ctx))) return rc;
+    if (op != MM_OP_DIV) return copy_out3(ctx, ctx->P.ihd, out);
+    CK_CUDA(cudaMemsetAsync(ctx->d_stage, 0, N * sizeof(double), ctx->stream));
+    k_scatter1<<<nblk(ctx->nphi), 256, 0, ctx->stream>>>(ctx->nphi, ctx->d_node_of_phi, ctx->d_ident, ctx->P.pq,
+                                                          ctx->d_stage);
+    CK_CUDA(cudaGetLastError());
+    CK_CUDA(cudaMemcpyAsync(out, ctx->d_stage, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK_CUDA(cudaStreamSynchronize(ctx->stream));
     return MM_OK;
 }

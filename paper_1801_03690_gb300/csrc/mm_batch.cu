@@ -170,6 +170,10 @@ void to_stats(const mm::DevState& s, double Mref, mm_stats* out) {
     for (int k = 0; k < 4; ++k) out->terms[k] = s.terms[k] * EJ;
     out->F_internal = s.F;
     for (int k = 0; k < 3; ++k) out->M[k] = s.M[k];
+    out->li2 = s.li2;
+    out->li2_first = s.li2_first;
+    out->restarts = s.restarts;
+    out->steepest = s.steepest;
 }
 
 int status_of(int st) {

@@ -28,6 +28,9 @@ enum Mode : int {
     MODE_PRECOND = 2,
     MODE_HESS = 3,
     MODE_KPHI = 4,
+    MODE_DIV = 5,
+    MODE_DIVT = 6,
+    MODE_LOCAL = 7,
 };
 
 enum DevStatus : int {
@@ -60,6 +63,7 @@ struct DevState {
     int cur;                 // index of the current slot
     int status;
     long long evals, nli, li, mi, ls_extra, mr;
+    long long li2, li2_first, restarts, steepest;   // branch counters (mm_stats)
     double F;                // internal units
     double terms[4];         // exchange, anisotropy, demag, Zeeman (internal)
     double M[3];             // weighted mean magnetisation of the current slot

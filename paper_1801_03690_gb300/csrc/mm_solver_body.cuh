@@ -316,6 +316,76 @@ __device__ __forceinline__ void sell_dot_2rows(const long long* __restrict__ spt
     for (int r = t.rank * MM_BLOCK + (int)threadIdx.x, r2 = 0; r < (n); r += 2 * t.nb * MM_BLOCK) \
         if (const bool two = ((r2 = r + t.nb * MM_BLOCK) < (n)); true)
 
+// ---- row kernels of the three operators of Eq. (energy) on the magnetic
+// graph, shared by the solver phases and the operator entry point.
+
+// (D x)_p of a magnetic row p (Sec. 3.1: the right-hand side of the
+// potential equation), x a SoA 3-vector over the magnetic nodes.
+__device__ __forceinline__ double row_div(const Problem& P, const double* x, int p) {
+    const int nm = P.nm;
+    const long long nz = P.nnzm;
+    const Row mr = sell_row(P.m_sptr, p);
+    double bp = 0.0;
+    for (int k0 = 0; k0 < mr.width; k0 += 8) {
+        int c[8];
+        double b0[8], b1[8], b2[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool ok = k0 + u < mr.width;
+            const long long e = mr.base + 32ll * (k0 + u);
+            c[u] = ok ? __ldg(P.m_col + e) : p;
+            b0[u] = ok ? __ldg(P.B + e) : 0.0;
+            b1[u] = ok ? __ldg(P.B + nz + e) : 0.0;
+            b2[u] = ok ? __ldg(P.B + 2 * nz + e) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bp += b0[u] * x[c[u]] + b1[u] * x[nm + c[u]] + b2[u] * x[2 * nm + c[u]];
+    }
+    return bp;
+}
+
+// (D^T phi)_i of a magnetic node i (the magnetostatic part of the gradient).
+__device__ __forceinline__ void row_divT(const Problem& P, const double* phi, int i, double& t0, double& t1,
+                                         double& t2) {
+    const long long nz = P.nnzm;
+    const Row rw = sell_row(P.m_sptr, i);
+    t0 = t1 = t2 = 0.0;
+    for (int k0 = 0; k0 < rw.width; k0 += 8) {
+        int c[8];
+        double q0[8], q1[8], q2[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool ok = k0 + u < rw.width;
+            const long long e = rw.base + 32ll * (k0 + u);
+            c[u] = ok ? __ldg(P.m_col + e) : i;
+            q0[u] = ok ? __ldg(P.G + e) : 0.0;
+            q1[u] = ok ? __ldg(P.G + nz + e) : 0.0;
+            q2[u] = ok ? __ldg(P.G + 2 * nz + e) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const double ph = phi[c[u]];
+            t0 += q0[u] * ph;
+            t1 += q1[u] * ph;
+            t2 += q2[u] * ph;
+        }
+    }
+}
+
+// The local operators at node i: c = K_A x (exchange stiffness on each
+// component; C_A x = 2 c) and a = C_K x (the lumped anisotropy block).
+__device__ __forceinline__ void row_local(const Problem& P, const double* x, int i, double& c0, double& c1,
+                                          double& c2, double& a0, double& a1, double& a2) {
+    const int nm = P.nm;
+    sell_dot3<8>(P.m_sptr, P.m_col, P.KA, x, nm, i, c0, c1, c2);
+    const double x0 = x[i], x1 = x[nm + i], x2 = x[2 * nm + i];
+    const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
+    const double kyy = P.CK[3 * nm + i], kyz = P.CK[4 * nm + i], kzz = P.CK[5 * nm + i];
+    a0 = kxx * x0 + kxy * x1 + kxz * x2;
+    a1 = kxy * x0 + kyy * x1 + kyz * x2;
+    a2 = kxz * x0 + kyz * x1 + kzz * x2;
+}
+
 struct SlotScalars {
     double F, terms[4], gmax, dphi, xdiff, xmax, M[3];
 };
@@ -324,6 +394,7 @@ struct Ctx {
     const Problem* P;
     Team t;
     long long evals, nli, li, mi, ls_extra, mr;
+    long long li2, li2_first, restarts, steepest;
     double h[3];
     SlotScalars sl[MM_NSLOT];
     int y_is_g;
@@ -368,27 +439,11 @@ __device__ bool ph_pinit(Ctx& C, int s, double& bb, double& rz, double& rr) {
     const double* x = P.X[s];
     double acc[3] = {0.0, 0.0, 0.0};
     double dummy[1] = {0.0};
-    const long long nz = P.nnzm;
     ROWS(p, P.nphi) {
         const double kphi = sell_dot<8, double>(P.p_sptr, P.p_col, P.Kp, P.phi, p);
         double bp = 0.0;
         if (p < nm) {
-            const Row mr = sell_row(P.m_sptr, p);
-            for (int k0 = 0; k0 < mr.width; k0 += 8) {
-                int c[8];
-                double b0[8], b1[8], b2[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const bool ok = k0 + u < mr.width;
-                    const long long e = mr.base + 32ll * (k0 + u);
-                    c[u] = ok ? __ldg(P.m_col + e) : p;
-                    b0[u] = ok ? __ldg(P.B + e) : 0.0;
-                    b1[u] = ok ? __ldg(P.B + nz + e) : 0.0;
-                    b2[u] = ok ? __ldg(P.B + 2 * nz + e) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) bp += b0[u] * x[c[u]] + b1[u] * x[nm + c[u]] + b2[u] * x[2 * nm + c[u]];
-            }
+            bp = row_div(P, x, p);
             P.rhs[p] = bp;
         }
         const double r = bp - kphi;
@@ -873,7 +928,6 @@ __device__ bool ph_gradient(Ctx& C, int s, bool trial) {
     const Problem& P = *C.P;
     Team& t = C.t;
     const int nm = P.nm;
-    const long long nz = P.nnzm;
     const double* x = P.X[s];
     double* gr = P.GR[s];
     double* gp = P.GP[s];
@@ -888,38 +942,10 @@ __device__ bool ph_gradient(Ctx& C, int s, bool trial) {
         if (p < nm) {
             const int i = p;
             acc[3] += P.phi[i] * P.rhs[i];
-            double c0, c1, c2;
-            sell_dot3<8>(P.m_sptr, P.m_col, P.KA, x, nm, i, c0, c1, c2);
-            double t0 = 0, t1 = 0, t2 = 0;
-            {
-                const Row rw = sell_row(P.m_sptr, i);
-                for (int k0 = 0; k0 < rw.width; k0 += 8) {
-                    int c[8];
-                    double q0[8], q1[8], q2[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const bool ok = k0 + u < rw.width;
-                        const long long e = rw.base + 32ll * (k0 + u);
-                        c[u] = ok ? __ldg(P.m_col + e) : i;
-                        q0[u] = ok ? __ldg(P.G + e) : 0.0;
-                        q1[u] = ok ? __ldg(P.G + nz + e) : 0.0;
-                        q2[u] = ok ? __ldg(P.G + 2 * nz + e) : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const double ph = P.phi[c[u]];
-                        t0 += q0[u] * ph;
-                        t1 += q1[u] * ph;
-                        t2 += q2[u] * ph;
-                    }
-                }
-            }
+            double c0, c1, c2, a0, a1, a2, t0, t1, t2;
+            row_local(P, x, i, c0, c1, c2, a0, a1, a2);
+            row_divT(P, P.phi, i, t0, t1, t2);
             const double x0 = x[i], x1 = x[nm + i], x2 = x[2 * nm + i];
-            const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
-            const double kyy = P.CK[3 * nm + i], kyz = P.CK[4 * nm + i], kzz = P.CK[5 * nm + i];
-            const double a0 = kxx * x0 + kxy * x1 + kxz * x2;
-            const double a1 = kxy * x0 + kyy * x1 + kyz * x2;
-            const double a2 = kxz * x0 + kyz * x1 + kzz * x2;
             const double wi = P.w[i];
             const double g0 = 2.0 * c0 + a0 + t0 - wi * h0;
             const double g1 = 2.0 * c1 + a1 + t1 - wi * h1;
@@ -1009,14 +1035,12 @@ __device__ bool ph_hess(Ctx& C, int s, const double* v, double ca, double beta, 
     double acc[1] = {0.0};
     double dummy[1] = {0.0};
     ROWS(i, nm) {
-        double c0, c1, c2;
-        sell_dot3<8>(P.m_sptr, P.m_col, P.KA, v, nm, i, c0, c1, c2);
+        double c0, c1, c2, k0, k1, k2;
+        row_local(P, v, i, c0, c1, c2, k0, k1, k2);
         const double v0 = v[i], v1 = v[nm + i], v2 = v[2 * nm + i];
-        const double kxx = P.CK[i], kxy = P.CK[nm + i], kxz = P.CK[2 * nm + i];
-        const double kyy = P.CK[3 * nm + i], kyz = P.CK[4 * nm + i], kzz = P.CK[5 * nm + i];
-        const double Cv0 = 2.0 * c0 + (kxx * v0 + kxy * v1 + kxz * v2);
-        const double Cv1 = 2.0 * c1 + (kxy * v0 + kyy * v1 + kyz * v2);
-        const double Cv2 = 2.0 * c2 + (kxz * v0 + kyz * v1 + kzz * v2);
+        const double Cv0 = 2.0 * c0 + k0;
+        const double Cv1 = 2.0 * c1 + k1;
+        const double Cv2 = 2.0 * c2 + k2;
         const double m0 = m[i], m1 = m[nm + i], m2 = m[2 * nm + i];
         const double mc = m0 * Cv0 + m1 * Cv1 + m2 * Cv2;
         const double lam = lamv[i];
@@ -1055,6 +1079,36 @@ __device__ bool ph_hess(Ctx& C, int s, const double* v, double ca, double beta, 
     if (!team_reduce<1, 0>(t, acc, dummy)) return false;
     dHd = acc[0];
     return true;
+}
+
+// One application of an operator of Eq. (energy) (the operator entry
+// point): MODE_DIV q = D v (v: idir[0], 3 x nm; q: pq, n_phi, zero on the
+// air rows), MODE_DIVT w = D^T phi (phi: pdir[0]; w: ihd), MODE_LOCAL
+// w = (C_A + C_K) v (v: idir[0]; w: ihd).
+__device__ bool ph_operator(Ctx& C, int mode) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    if (mode == MODE_DIV) {
+        ROWS(p, P.nphi) P.pq[p] = (p < nm) ? row_div(P, P.idir[0], p) : 0.0;
+    } else if (mode == MODE_DIVT) {
+        ROWS(i, nm) {
+            double t0, t1, t2;
+            row_divT(P, P.pdir[0], i, t0, t1, t2);
+            P.ihd[i] = t0;
+            P.ihd[nm + i] = t1;
+            P.ihd[2 * nm + i] = t2;
+        }
+    } else {
+        ROWS(i, nm) {
+            double c0, c1, c2, a0, a1, a2;
+            row_local(P, P.idir[0], i, c0, c1, c2, a0, a1, a2);
+            P.ihd[i] = 2.0 * c0 + a0;
+            P.ihd[nm + i] = 2.0 * c1 + a1;
+            P.ihd[2 * nm + i] = 2.0 * c2 + a2;
+        }
+    }
+    return team_sync(t);
 }
 
 // Algorithm 1 for H(m_s) y = g_s, y_0 = 0, Jacobi diag(C_A), exits li1-li3.
@@ -1099,7 +1153,11 @@ __device__ bool precond_solve(Ctx& C, int s) {
         ++steps;
         C.li++;
         if (dHd <= 0.0) {                       // li2
-            if (steps == 1) C.y_is_g = 1;
+            C.li2++;
+            if (steps == 1) {
+                C.y_is_g = 1;
+                C.li2_first++;
+            }
             return true;
         }
         const double a = gy / dHd;
@@ -1202,6 +1260,7 @@ __device__ bool direction(Ctx& C, int a, int c, bool initial, double& dmax, doub
         if (gd >= 0.0) {
             kind = 3;
             gd = -gn_gn;
+            C.steepest++;
         }
     } else {
         beta = beta_za(y_gn, y_go, dg_y, dg_d);
@@ -1210,10 +1269,12 @@ __device__ bool direction(Ctx& C, int a, int c, bool initial, double& dmax, doub
             beta = beta_za(gn_gn, gn_go, dg_gn, dg_d);
             kind = 2;
             gd = -gn_gn + beta * gn_d;
+            C.restarts++;
             if (gd >= 0.0) {
                 kind = 3;
                 beta = 0.0;
                 gd = -gn_gn;
+                C.steepest++;
             }
         }
     }
@@ -1324,6 +1385,7 @@ __device__ __forceinline__ void solver_body(const Problem& P, int nb, int rank) 
     C.t.epoch = 0;
     C.t.dead = false;
     C.evals = C.nli = C.li = C.mi = C.ls_extra = C.mr = 0;
+    C.li2 = C.li2_first = C.restarts = C.steepest = 0;
     C.y_is_g = 0;
     int cur = P.state->cur;
     C.h[0] = P.state->h[0];
@@ -1351,6 +1413,11 @@ __device__ __forceinline__ void solver_body(const Problem& P, int nb, int rank) 
             if (!ph_pmatvec(C, P.pdir[0], P.pq)) status = ST_TIMEOUT;
             break;
         }
+        case MODE_DIV:
+        case MODE_DIVT:
+        case MODE_LOCAL:
+            if (!ph_operator(C, P.mode)) status = ST_TIMEOUT;
+            break;
         default:
             status = ST_TIMEOUT;
     }
@@ -1365,6 +1432,10 @@ __device__ __forceinline__ void solver_body(const Problem& P, int nb, int rank) 
         st->mi = C.mi;
         st->ls_extra = C.ls_extra;
         st->mr = C.mr;
+        st->li2 = C.li2;
+        st->li2_first = C.li2_first;
+        st->restarts = C.restarts;
+        st->steepest = C.steepest;
         if (P.mode == MODE_MINIMIZE || P.mode == MODE_EVAL) {
             const SlotScalars& S = C.sl[cur];
             st->F = S.F;

@@ -107,3 +107,27 @@ def test_amg_matches_jacobi_form_on_a_jittered_cube(lib):
     assert s0["status"] == "ok" and s1["status"] == "ok"
     assert s1["F"] == pytest.approx(s0["F"], rel=1e-8)
     assert np.abs(m1 - m0).max() < 1e-5
+
+
+def test_amg_two_level_minimize_matches_oracle(lib):
+    """The multigrid precision form on the cube whose hierarchy has two
+    smoothed levels (24^3 voxels, 103,823 potential unknowns), minimised at
+    one field from m0, against the oracle's Algorithm 4 (energy 1e-8, max
+    nodal |dm| 1e-5)."""
+    Magnet, Params, _ = lib
+    wl = synth.hard_cube(n_mag=24)
+    P = fem.assemble_workload(wl)
+    b = wl.fields[3]
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    assert len(mag.amg_levels()) == 3
+    mag.set_magnetization(wl.m0)
+    mag.set_field(b)
+    st = mag.minimize(Params(jmax=4, precision=1, amg=1, inner_tol=1e-3, poisson_tol=1e-12))
+    m = mag.get_magnetization()[P.mag_nodes]
+    r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=4, poisson="cg", poisson_tol=1e-12))
+    assert st["status"] == "ok" and r.status == "converged"
+    assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+    assert np.abs(m - r.m).max() < 1e-5
+    mag.close()

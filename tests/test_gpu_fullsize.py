@@ -1,9 +1,10 @@
-"""Parity at the benchmark's full size (80 nm hard-magnet cube, 48^3
-voxels, 857,375 potential unknowns) in the launch configuration bench.py
-times: sampled rows of the potential stiffness against the oracle
+"""Parity at full size for the 80 nm hard-magnet cube (48^3 voxels,
+857,375 potential unknowns; its full demagnetisation curve is part of the
+bench line): sampled rows of the potential stiffness against the oracle
 assembled on the sampled nodes' neighbourhoods, closed-form energies of
-uniform states, and the converged first field step against the
-properties of a minimum."""
+uniform states, the converged first field step against the properties of
+a minimum, and one field step of both GPU forms against the oracle's own
+minimisation at this size."""
 import numpy as np
 import pytest
 
@@ -117,3 +118,47 @@ def test_multigrid_form_first_field_step_matches_jacobi_form(full):
     g = mag.gradient(None, projected=True, params=Params(precision=1, amg=1, inner_tol=1e-3))
     assert np.abs(g).max() < 1e-10 ** (1 / 3) * (1 + abs(sm["F_internal"]))
     assert sm["mi"] / sm["evals"] < 0.25 * sj["mi"] / sj["evals"]
+
+
+@pytest.mark.parametrize("form", ["plain_fp64", "multigrid_precision"])
+def test_field_step_matches_oracle_minimization(full, form):
+    """One field step of the curve (field index 1, from m0) at full size:
+    the GPU plain FP64 form and the multigrid precision form against the
+    oracle's Algorithm 4 with its own Jacobi-CG potential solve on the same
+    mesh: energy 1e-8 relative, max nodal |dm| 1e-5; the FP64 form along the
+    same path (same iteration, evaluation and inner-step counts)."""
+    from paper_1801_03690_gb300 import Params
+    from oracle import energy, ncg
+    wl, mag = full
+    P = _oracle_full(wl)
+    b = wl.fields[1]
+    prm = (Params(jmax=4, poisson_tol=1e-10) if form == "plain_fp64"
+           else Params(jmax=4, poisson_tol=1e-10, precision=1, amg=1, inner_tol=1e-3))
+    mag.set_magnetization(wl.m0)
+    mag.set_field(b)
+    st = mag.minimize(prm)
+    m = mag.get_magnetization()[P.mag_nodes]
+    r = _oracle_step(P, wl)
+    assert st["status"] == "ok" and r.status == "converged"
+    assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+    assert np.abs(m - r.m).max() < 1e-5
+    if form == "plain_fp64":
+        for k in ("nli", "evals", "li", "ls_extra"):
+            assert st[k] == r.stats[k], (k, st[k], r.stats[k])
+
+
+_ORACLE = {}
+
+
+def _oracle_full(wl):
+    if "P" not in _ORACLE:
+        _ORACLE["P"] = fem.assemble_workload(wl)
+    return _ORACLE["P"]
+
+
+def _oracle_step(P, wl):
+    from oracle import energy, ncg
+    if "r" not in _ORACLE:
+        _ORACLE["r"] = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(wl.fields[1]),
+                                    ncg.Params(jmax=4, poisson="cg", poisson_tol=1e-10))
+    return _ORACLE["r"]

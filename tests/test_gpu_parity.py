@@ -37,6 +37,18 @@ def _hard(n_mag=6, jitter=0.07, seed=4, box=2.0):
                             K1=4.3e6, axis=(np.sin(t), 0.2, np.cos(t)), jitter=jitter, seed=seed)
 
 
+PATH_COUNTERS = ("nli", "evals", "li", "ls_extra", "li2", "li2_first", "restarts", "steepest")
+
+
+def _same_path(st, r):
+    """Parity along the same path: every counter of Algorithm 4's branches
+    (iterations, evaluations, inner steps, backtracking evaluations, li2
+    exits, safeguard restarts and steepest-descent fallbacks) equals the
+    oracle's."""
+    for k in PATH_COUNTERS:
+        assert st[k] == r.stats[k], (k, st[k], r.stats[k])
+
+
 def test_sizes_match_oracle(lib):
     wl = _hard()
     mag, P = _setup(lib, wl)
@@ -148,6 +160,7 @@ def test_minimize_parity_soft(lib, jmax):
     assert st["status"] == "ok" and r.status == "converged"
     assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
     assert np.abs(m - r.m).max() < 1e-5
+    _same_path(st, r)
     np.testing.assert_allclose(np.linalg.norm(m, axis=1), 1.0, atol=1e-14)
     assert st["evals"] == 2 * st["nli"] + 1 + st["ls_extra"]
     assert st["li"] <= jmax * (st["nli"] + 1)
@@ -236,6 +249,8 @@ def test_soft_cube_first_field_step(lib, prec, amg):
     assert st["status"] == "ok" and r.status == "converged"
     assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
     assert np.abs(m - r.m).max() < 1e-5
+    if prec == 0:
+        _same_path(st, r)
 
 
 @pytest.mark.parametrize("psi_deg", [20.0, 45.0, 70.0])
@@ -261,4 +276,47 @@ def test_stoner_wohlfarth_astroid_on_gpu(lib, psi_deg):
         m = mag.get_magnetization()
         mz = m[np.linalg.norm(m, axis=1) > 0, 2]
         assert (mz.mean() < 0) == switched
+    mag.close()
+
+
+def _anti(n_mag, b, seed=0):
+    """A hard cube magnetised against a strong field (m ~ -z, field +z): the
+    approximate Hessian is indefinite there, so the preconditioner solve
+    exits by negative curvature (li2), on its first step too (y = g), and
+    the descent safeguard restarts the direction and falls back to -g."""
+    wl = _hard(n_mag=n_mag)
+    rng = np.random.default_rng(seed)
+    m0 = -np.tile([0.0, 0.0, 1.0], (wl.mesh.n_nodes, 1)) + 0.05 * rng.standard_normal((wl.mesh.n_nodes, 3))
+    return wl, m0, np.asarray(b, dtype=np.float64)
+
+
+@pytest.mark.parametrize("case", ["negative_curvature_and_safeguard", "backtracking"])
+def test_rare_branches_fire_and_match_oracle(lib, case):
+    """The rare branches of Algorithm 4 fire on the GPU and the path equals
+    the oracle's: 16 iterations of the anti-parallel cube (li2 on the first
+    and later inner steps, a safeguard restart and a steepest-descent
+    fallback), and 12 iterations with the sufficient-decrease constant
+    c1 = 0.99, under which the cubic step fails the test and the line search
+    backtracks."""
+    Magnet, Params = lib
+    if case == "backtracking":
+        wl = _hard(n_mag=4)
+        m0, b, it, extra = wl.m0, np.array([0.1, 0.0, 0.5]), 12, dict(c1=0.99)
+    else:
+        wl, m0, b = _anti(3, [0.0, 0.0, 6.0])
+        it, extra = 16, {}
+    mag, P = _setup(lib, wl)
+    mag.set_magnetization(m0)
+    mag.set_field(b)
+    st = mag.minimize(Params(jmax=4, max_iter=it, **TIGHT, **extra))
+    r = ncg.minimize(P, energy.normalize(m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=4, max_iter=it, **extra))
+    assert st["status"] == "not_converged" and r.status == "max_iter"
+    _same_path(st, r)
+    if case == "backtracking":
+        assert st["ls_extra"] > 0
+    else:
+        assert st["li2"] > 0 and st["li2_first"] > 0 and st["restarts"] > 0 and st["steepest"] > 0
+    assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+    assert np.abs(mag.get_magnetization()[P.mag_nodes] - r.m).max() < 1e-5
     mag.close()
