@@ -663,10 +663,10 @@ def curve_mode(args, rank, local_rank):
         coarse = synth.hard_cube(n_mag=12, seed=12, n_fields=len(fields))
     tm = Magnet(device=local_rank)
     tm.upload_workload(coarse)
-    X, T, _ = warmstart.collect(tm, coarse.m0, coarse.fields, tm.sizes()["n_mag"],
+    net = MLP(device=local_rank, seed=11)
+    X, T, _ = warmstart.collect(tm, net, coarse.m0, coarse.fields, tm.sizes()["n_mag"],
                                 Params(precision=1, amg=1, inner_tol=1e-3))
     tm.close()
-    net = MLP(device=local_rank, seed=11)
     s_m, s_p, losses = warmstart.train(net, X, T, steps=1500, batch=16384, lr=2e-3, log_every=500)
     train_s = time.perf_counter() - t0
     run("precision_learned", Params(precision=1, amg=1, inner_tol=1e-3, theta_max=args.theta_max), net=net,

@@ -362,6 +362,28 @@ int mm_mlp_gradient(mm_mlp* mlp, const float* X_dev, const float* T_dev, int64_t
  * be NULL (then no synchronisation). */
 int mm_mlp_train_step(mm_mlp* mlp, const float* X_dev, const float* T_dev, int64_t n,
                       float lr, float* loss_out);
+/* Set the input standardisation from data: per feature, the mean and the
+ * unbiased standard deviation of X_dev [n][16] (device, FP64 sums, blocks
+ * in a fixed order); a feature whose deviation is below 1e-6 (|mean| + 1)
+ * is only centred.  n >= 2.  mm_mlp_get_input_norm reads back the mean and
+ * 1/std in use. */
+int mm_mlp_fit_input_norm(mm_mlp* mlp, const float* X_dev, int64_t n);
+int mm_mlp_get_input_norm(mm_mlp* mlp, float mean[16], float inv_stdev[16]);
+/* Target scales for training: *scale_m = the unbiased standard deviation of
+ * the m-columns T[:, 0:3] taken together, *scale_phi that of T[:, 3] (each
+ * at least 1e-12), and Tn_dev [n][4] = T_dev with those columns divided by
+ * them (device arrays; Tn_dev may be T_dev).  n >= 2. */
+int mm_mlp_fit_target_scales(mm_mlp* mlp, const float* T_dev, int64_t n, float* Tn_dev, double* scale_m,
+                             double* scale_phi);
+/* Training targets of one field step from the features of the converged
+ * states before (X0_dev) and after (X1_dev) it, both [n][16] from
+ * mm_warmstart_features for the same step: T_dev [n][4] = (m_after -
+ * m_before, phi_after - phi_before) / |dh|, |dh| the norm of the field
+ * increment (features 12..14, internal units).  *dh_out = |dh| (0: T_dev
+ * left untouched); *max_change_out = the largest nodal |m_after - m_before|
+ * (a switching step shows as a large value). */
+int mm_warmstart_targets(mm_mlp* mlp, const float* X0_dev, const float* X1_dev, int64_t n, float* T_dev,
+                         double* dh_out, double* max_change_out);
 /* Features of every magnetic node of the context's current state for the
  * step to the applied field mu0h_next (tesla): m, effective field, exchange
  * field, anisotropy field (fields per unit Ms weight, internal units), the

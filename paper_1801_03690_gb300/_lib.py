@@ -107,6 +107,12 @@ EXPORTS = {
                                   C.POINTER(C.c_float)]),
     "mm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
                                     C.POINTER(C.c_float)]),
+    "mm_mlp_fit_input_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "mm_mlp_get_input_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mm_mlp_fit_target_scales": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mm_warmstart_targets": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mm_warmstart_features": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "mm_warmstart_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_double,
                                      C.c_double, C.c_double]),

@@ -412,6 +412,51 @@ class MLP:
         if rc:
             raise MMError(rc, "mm_mlp_set_input_norm")
 
+    def fit_input_norm(self, X):
+        """Input standardisation from the data X [n, 16] (float32, device)."""
+        assert X.is_cuda and X.is_contiguous() and X.shape[1] == 16
+        rc = self._lib.mm_mlp_fit_input_norm(self._h, C.c_void_p(X.data_ptr()), X.shape[0])
+        if rc:
+            raise MMError(rc, "mm_mlp_fit_input_norm")
+
+    def input_norm(self):
+        """(mean, 1/std) in use, float32 arrays of 16."""
+        m = np.zeros(16, dtype=np.float32)
+        s = np.zeros(16, dtype=np.float32)
+        rc = self._lib.mm_mlp_get_input_norm(self._h, m.ctypes.data_as(C.c_void_p), s.ctypes.data_as(C.c_void_p))
+        if rc:
+            raise MMError(rc, "mm_mlp_get_input_norm")
+        return m, s
+
+    def fit_target_scales(self, T):
+        """(Tn, scale_m, scale_phi): T [n, 4] (float32, device) with its m and
+        potential columns divided by their standard deviations."""
+        import torch
+        assert T.is_cuda and T.is_contiguous() and T.shape[1] == 4
+        Tn = torch.empty_like(T)
+        sm = C.c_double()
+        sp = C.c_double()
+        rc = self._lib.mm_mlp_fit_target_scales(self._h, C.c_void_p(T.data_ptr()), T.shape[0],
+                                                C.c_void_p(Tn.data_ptr()), C.byref(sm), C.byref(sp))
+        if rc:
+            raise MMError(rc, "mm_mlp_fit_target_scales")
+        return Tn, sm.value, sp.value
+
+    def step_targets(self, X0, X1):
+        """(T, |dh|, largest nodal change) of one field step from the
+        features before and after it (mm_warmstart_targets); T is None when
+        the field did not change."""
+        import torch
+        assert X0.shape == X1.shape and X0.shape[1] == 16 and X0.is_contiguous() and X1.is_contiguous()
+        T = torch.empty((X0.shape[0], 4), dtype=torch.float32, device=X0.device)
+        dh = C.c_double()
+        mx = C.c_double()
+        rc = self._lib.mm_warmstart_targets(self._h, C.c_void_p(X0.data_ptr()), C.c_void_p(X1.data_ptr()),
+                                            X0.shape[0], C.c_void_p(T.data_ptr()), C.byref(dh), C.byref(mx))
+        if rc:
+            raise MMError(rc, "mm_warmstart_targets")
+        return (T if dh.value > 0 else None), dh.value, mx.value
+
     def get_params(self):
         f = np.zeros(self.n_params, dtype=np.float32)
         rc = self._lib.mm_mlp_get_params(self._h, f.ctypes.data_as(C.c_void_p), f.size)

@@ -531,6 +531,84 @@ __global__ void k_apply(int nm, const mm::Problem* Pp, const mm::DevState* st, c
 
 }  // namespace
 
+// Training targets from two consecutive converged states' features (rows
+// of X0 at field k, X1 at field k+1): T_i = (m_{k+1} - m_k, phi_{k+1} -
+// phi_k) / |dh| (features 0..2 are m, 15 the potential); the largest nodal
+// change |m_{k+1} - m_k| goes to mx (non-negative floats compare like their
+// bit patterns).
+__global__ void k_ws_targets(long long n, const float* __restrict__ X0, const float* __restrict__ X1, float inv_dh,
+                             float* __restrict__ T, unsigned* mx) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float c = 0.0f;
+    if (i < n) {
+        const float* a = X0 + i * NIN;
+        const float* b = X1 + i * NIN;
+        const float d0 = b[0] - a[0], d1 = b[1] - a[1], d2 = b[2] - a[2];
+        T[i * NOUT] = d0 * inv_dh;
+        T[i * NOUT + 1] = d1 * inv_dh;
+        T[i * NOUT + 2] = d2 * inv_dh;
+        T[i * NOUT + 3] = (b[15] - a[15]) * inv_dh;
+        c = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    for (int o = 16; o > 0; o >>= 1) c = fmaxf(c, __shfl_down_sync(0xffffffffu, c, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, __float_as_uint(c));
+}
+
+// Column statistics of an [n][w] float array (columns c0 .. c0+nc-1, or all
+// nc columns pooled when pool = 1): FP64 sums per block in a fixed order,
+// written to part[block][2 * nc]: sum of x - shift and of (x - shift)^2.
+__global__ void k_colstats(long long n, int w, int c0, int nc, int pool, const float* __restrict__ X,
+                           const double* __restrict__ shift, double* __restrict__ part) {
+    __shared__ double sh[2][16][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = 0; c < nc; ++c) {
+        double s1 = 0.0, s2 = 0.0;
+        const double sc = shift[pool ? 0 : c];
+        for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+            if (pool) {
+                for (int q = 0; q < nc; ++q) {
+                    const double x = (double)X[r * w + c0 + q] - sc;
+                    s1 += x;
+                    s2 += x * x;
+                }
+            } else {
+                const double x = (double)X[r * w + c0 + c] - sc;
+                s1 += x;
+                s2 += x * x;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+            s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            sh[0][c][warp] = s1;
+            sh[1][c][warp] = s2;
+        }
+        if (pool) break;
+    }
+    __syncthreads();
+    const int nout = pool ? 1 : nc;
+    if (threadIdx.x < nout) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            a += sh[0][threadIdx.x][q];
+            b += sh[1][threadIdx.x][q];
+        }
+        part[(size_t)blockIdx.x * 2 * nout + threadIdx.x] = a;
+        part[(size_t)blockIdx.x * 2 * nout + nout + threadIdx.x] = b;
+    }
+}
+
+__global__ void k_scale_targets(long long n, const float* __restrict__ T, float sm, float sp, float* __restrict__ Tn) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Tn[i * NOUT] = T[i * NOUT] / sm;
+    Tn[i * NOUT + 1] = T[i * NOUT + 1] / sm;
+    Tn[i * NOUT + 2] = T[i * NOUT + 2] / sm;
+    Tn[i * NOUT + 3] = T[i * NOUT + 3] / sp;
+}
+
 struct mm_mlp {
     int device = 0;
     int nsm = 0;
@@ -782,6 +860,134 @@ int mm_mlp_train_step(mm_mlp* M, const float* X_dev, const float* T_dev, int64_t
         MK(cudaMemcpyAsync(loss_out, M->loss, sizeof(float), cudaMemcpyDeviceToHost, M->stream));
         MK(cudaStreamSynchronize(M->stream));
     }
+    return MM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Mean and unbiased standard deviation of columns c0 .. c0+nc-1 of an [n][w]
+// device array (pool = 1: all nc columns together), FP64, two passes (the
+// second about the first pass's mean), blocks reduced in a fixed order.
+int col_mean_std(mm_mlp* M, const float* X, long long n, int w, int c0, int nc, int pool, double* mean,
+                 double* sd) {
+    const int nb = std::max(1, std::min((int)((n + 255) / 256), 4 * M->nsm));
+    const int nout = pool ? 1 : nc;
+    double *dpart = nullptr, *dshift = nullptr;
+    MK(cudaMalloc(&dpart, (size_t)nb * 2 * nout * sizeof(double)));
+    if (cudaMalloc(&dshift, 16 * sizeof(double)) != cudaSuccess) {
+        cudaFree(dpart);
+        return MM_ERR_OOM;
+    }
+    std::vector<double> shift(16, 0.0), part((size_t)nb * 2 * nout);
+    const double cnt = (double)n * (pool ? nc : 1);
+    int rc = MM_OK;
+    for (int pass = 0; pass < 2 && rc == MM_OK; ++pass) {
+        if (cudaMemcpy(dshift, shift.data(), 16 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = MM_ERR_CUDA;
+            break;
+        }
+        k_colstats<<<nb, 256, 0, M->stream>>>(n, w, c0, nc, pool, X, dshift, dpart);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(M->stream) != cudaSuccess ||
+            cudaMemcpy(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = MM_ERR_CUDA;
+            break;
+        }
+        for (int c = 0; c < nout; ++c) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int b = 0; b < nb; ++b) {
+                s1 += part[(size_t)b * 2 * nout + c];
+                s2 += part[(size_t)b * 2 * nout + nout + c];
+            }
+            if (pass == 0) {
+                shift[c] = s1 / cnt;                       // the mean
+            } else {
+                mean[c] = shift[c] + s1 / cnt;
+                sd[c] = cnt > 1 ? std::sqrt(std::max(0.0, (s2 - s1 * s1 / cnt) / (cnt - 1.0))) : 0.0;
+            }
+        }
+    }
+    cudaFree(dpart);
+    cudaFree(dshift);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mm_mlp_fit_input_norm(mm_mlp* M, const float* X_dev, int64_t n) {
+    if (!M || !X_dev || n < 2) return MM_ERR_ARG;
+    MK(cudaSetDevice(M->device));
+    MK(cudaStreamSynchronize(M->stream));
+    double mean[NIN], sd[NIN];
+    int rc = col_mean_std(M, X_dev, n, NIN, 0, NIN, 0, mean, sd);
+    if (rc) return rc;
+    float h[2 * NIN];
+    for (int i = 0; i < NIN; ++i) {
+        if (!std::isfinite(mean[i]) || !std::isfinite(sd[i])) return MM_ERR_NONFINITE;
+        const double s = (sd[i] > 1e-6 * (std::fabs(mean[i]) + 1.0)) ? sd[i] : 1.0;   // constant: centre only
+        h[i] = (float)mean[i];
+        h[NIN + i] = (float)(1.0 / s);
+    }
+    MK(cudaMemcpy(M->norm, h, sizeof(h), cudaMemcpyHostToDevice));
+    return MM_OK;
+}
+
+int mm_mlp_get_input_norm(mm_mlp* M, float* mean, float* inv_stdev) {
+    if (!M || !mean || !inv_stdev) return MM_ERR_ARG;
+    MK(cudaSetDevice(M->device));
+    MK(cudaStreamSynchronize(M->stream));
+    float h[2 * NIN];
+    MK(cudaMemcpy(h, M->norm, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < NIN; ++i) {
+        mean[i] = h[i];
+        inv_stdev[i] = h[NIN + i];
+    }
+    return MM_OK;
+}
+
+int mm_mlp_fit_target_scales(mm_mlp* M, const float* T_dev, int64_t n, float* Tn_dev, double* scale_m,
+                             double* scale_phi) {
+    if (!M || !T_dev || !Tn_dev || !scale_m || !scale_phi || n < 2) return MM_ERR_ARG;
+    MK(cudaSetDevice(M->device));
+    MK(cudaStreamSynchronize(M->stream));
+    double mm_[1], sm[1], mp[1], sp[1];
+    int rc = col_mean_std(M, T_dev, n, NOUT, 0, 3, 1, mm_, sm);
+    if (rc) return rc;
+    if ((rc = col_mean_std(M, T_dev, n, NOUT, 3, 1, 0, mp, sp))) return rc;
+    if (!std::isfinite(sm[0]) || !std::isfinite(sp[0])) return MM_ERR_NONFINITE;
+    *scale_m = std::max(sm[0], 1e-12);
+    *scale_phi = std::max(sp[0], 1e-12);
+    k_scale_targets<<<(unsigned)((n + 255) / 256), 256, 0, M->stream>>>(n, T_dev, (float)*scale_m, (float)*scale_phi,
+                                                                       Tn_dev);
+    MK(cudaGetLastError());
+    MK(cudaStreamSynchronize(M->stream));
+    return MM_OK;
+}
+
+int mm_warmstart_targets(mm_mlp* M, const float* X0_dev, const float* X1_dev, int64_t n, float* T_dev,
+                         double* dh_out, double* max_change_out) {
+    if (!M || !X0_dev || !X1_dev || !T_dev || !dh_out || !max_change_out || n < 1) return MM_ERR_ARG;
+    MK(cudaSetDevice(M->device));
+    MK(cudaStreamSynchronize(M->stream));
+    float inc[3];
+    MK(cudaMemcpy(inc, X0_dev + 12, 3 * sizeof(float), cudaMemcpyDeviceToHost));   // the field increment
+    const double dh = std::sqrt((double)inc[0] * inc[0] + (double)inc[1] * inc[1] + (double)inc[2] * inc[2]);
+    *dh_out = dh;
+    *max_change_out = 0.0;
+    if (!(dh > 0.0)) return MM_OK;
+    MK(cudaMemsetAsync(M->d_max, 0, sizeof(unsigned), M->stream));
+    k_ws_targets<<<(unsigned)((n + 255) / 256), 256, 0, M->stream>>>(n, X0_dev, X1_dev, (float)(1.0 / dh), T_dev,
+                                                                     M->d_max);
+    MK(cudaGetLastError());
+    unsigned mx = 0;
+    MK(cudaMemcpyAsync(&mx, M->d_max, sizeof(unsigned), cudaMemcpyDeviceToHost, M->stream));
+    MK(cudaStreamSynchronize(M->stream));
+    float f;
+    std::memcpy(&f, &mx, sizeof(f));
+    *max_change_out = f;
     return MM_OK;
 }
 

@@ -7,19 +7,23 @@ state).
 Training pairs: at the converged state of field step k, the features for the
 step to field k+1 (mm_warmstart_features) and the targets
 ((m_{k+1} - m_k), (phi_{k+1} - phi_k)) / |dh| on the magnetic nodes, where
-|dh| is the norm of the field increment in internal units.  The network
-standardises its inputs itself (FP32, before the BF16 first layer;
-features such as m_z = 0.999 +- 0.001 would lose their signal if the
-standardisation were folded into BF16 weights); targets are standardised
-for training and their scales become the scale_m / scale_phi arguments of
-mm_warmstart_apply.
+|dh| is the norm of the field increment in internal units
+(mm_warmstart_targets).  The network standardises its inputs itself (FP32,
+before the BF16 first layer; features such as m_z = 0.999 +- 0.001 would
+lose their signal if the standardisation were folded into BF16 weights);
+the statistics (mm_mlp_fit_input_norm) and the target scales
+(mm_mlp_fit_target_scales), which become the scale_m / scale_phi arguments
+of mm_warmstart_apply, are computed by the library.  This module only
+moves tensors: it concatenates the steps' arrays and draws the
+mini-batches.
 """
 from .api import Params, warmstart_features, warmstart_apply
 
 
-def collect(mag, m0, fields, n_mag, params=None, max_step_change=0.2):
-    """Run the curve on `mag` from m0 and return device tensors (X, T, nli).
-    Field steps on which some node turned by more than max_step_change
+def collect(mag, mlp, m0, fields, n_mag, params=None, max_step_change=0.2):
+    """Run the curve on `mag` from m0 and return device tensors (X, T, nli):
+    features and targets (mm_warmstart_targets) of every field step.  Field
+    steps on which some node turned by more than max_step_change
     (irreversible switching) are left out: the network is to learn the
     reversible response that keeps the state in its basin, not to jump."""
     import torch
@@ -33,29 +37,22 @@ def collect(mag, m0, fields, n_mag, params=None, max_step_change=0.2):
         mag.set_field(fields[k + 1])
         nli += mag.minimize(prm)["nli"]
         X1 = warmstart_features(mag, fields[k + 1], n_mag)
-        dh = float(torch.linalg.vector_norm(X[0, 12:15]).item())
-        if dh == 0.0:
+        T, dh, change = mlp.step_targets(X, X1)
+        if T is None or change > max_step_change:
             continue
-        if float(torch.linalg.vector_norm(X1[:, 0:3] - X[:, 0:3], dim=1).max().item()) > max_step_change:
-            continue
-        T = torch.cat([X1[:, 0:3] - X[:, 0:3], X1[:, 15:16] - X[:, 15:16]], dim=1) / dh
         Xs.append(X)
         Ts.append(T)
     return torch.cat(Xs), torch.cat(Ts), nli
 
 
 def train(mlp, X, T, steps=2000, batch=16384, lr=2e-3, seed=0, log_every=0):
-    """Set the network's input standardisation from X, train with Adam on
-    random mini-batches of standardised targets.  Returns
-    (scale_m, scale_phi, losses)."""
+    """Set the network's input standardisation from X and the target scales
+    from T (both computed by the library), then train with Adam on random
+    mini-batches of the standardised targets.  Returns (scale_m, scale_phi,
+    losses)."""
     import torch
-    mu = X.mean(0)
-    sd = X.std(0)
-    sd = torch.where(sd > 1e-6 * (mu.abs() + 1.0), sd, torch.ones_like(sd))   # constant features: centre only
-    mlp.set_input_norm(mu.cpu().numpy(), sd.cpu().numpy())
-    s_m = float(T[:, 0:3].std().clamp_min(1e-12).item())
-    s_p = float(T[:, 3].std().clamp_min(1e-12).item())
-    Tn = torch.cat([T[:, 0:3] / s_m, T[:, 3:4] / s_p], dim=1).contiguous()
+    mlp.fit_input_norm(X)
+    Tn, s_m, s_p = mlp.fit_target_scales(T)
     g = torch.Generator(device=X.device)
     g.manual_seed(seed)
     n = X.shape[0]

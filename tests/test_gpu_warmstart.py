@@ -86,8 +86,8 @@ def test_warm_start_gain_on_a_demag_curve():
     mag = Magnet()
     mag.upload_workload(train_wl)
     n_mag = mag.sizes()["n_mag"]
-    X, T, _ = warmstart.collect(mag, train_wl.m0, fields, n_mag, prm)
     net = MLP(seed=11)
+    X, T, _ = warmstart.collect(mag, net, train_wl.m0, fields, n_mag, prm)
     s_m, s_p, _ = warmstart.train(net, X, T, steps=600, batch=8192, lr=2e-3)
     mag.close()
     mag = Magnet()
@@ -101,3 +101,57 @@ def test_warm_start_gain_on_a_demag_curve():
     np.testing.assert_allclose(Mw, Mb, atol=1e-4)
     print(f"NCG iterations without / with the warm start: {nli_base} / {nli_warm}")
     assert nli_warm < nli_base
+
+
+def test_library_training_statistics_match_their_definitions():
+    """The warm start's data arithmetic runs in the library: the input
+    standardisation (mean and unbiased standard deviation per feature; a
+    constant feature is only centred), the target scales (standard
+    deviation of the m columns together and of the potential column) with
+    the scaled targets, and a field step's targets ((after - before) / |dh|
+    and the largest nodal change), against numpy in FP64."""
+    import torch
+    from paper_1801_03690_gb300 import MLP
+    net = MLP(seed=3)
+    rng = np.random.default_rng(12)
+    n = 50000
+    Xh = rng.normal(size=(n, 16)) * rng.uniform(0.1, 5.0, 16) + rng.uniform(-3, 3, 16)
+    Xh[:, 4] = 0.75                                   # constant feature
+    Xh[:, 5] = 0.999 + 1e-3 * rng.normal(size=n)      # small spread on a large mean
+    Xh = Xh.astype(np.float32)
+    X = torch.tensor(Xh, device="cuda")
+    net.fit_input_norm(X)
+    mean, inv_sd = net.input_norm()
+    x64 = Xh.astype(np.float64)
+    mu, sd = x64.mean(0), x64.std(0, ddof=1)
+    sd = np.where(sd > 1e-6 * (np.abs(mu) + 1.0), sd, 1.0)
+    np.testing.assert_allclose(mean, mu, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(inv_sd, 1.0 / sd, rtol=1e-6)
+    assert inv_sd[4] == 1.0
+
+    Th = (rng.normal(size=(n, 4)) * np.array([0.01, 0.02, 0.03, 5.0])).astype(np.float32)
+    T = torch.tensor(Th, device="cuda")
+    Tn, s_m, s_p = net.fit_target_scales(T)
+    t64 = Th.astype(np.float64)
+    assert s_m == pytest.approx(t64[:, :3].reshape(-1).std(ddof=1), rel=1e-9)
+    assert s_p == pytest.approx(t64[:, 3].std(ddof=1), rel=1e-9)
+    ref = np.concatenate([Th[:, :3] / np.float32(s_m), Th[:, 3:] / np.float32(s_p)], axis=1)
+    np.testing.assert_allclose(Tn.cpu().numpy(), ref, rtol=1e-6)
+
+    X1h = Xh.copy()
+    X1h[:, 0:3] += (1e-3 * rng.normal(size=(n, 3))).astype(np.float32)
+    X1h[:, 15] += (0.1 * rng.normal(size=n)).astype(np.float32)
+    X1h[777, 0:3] += np.float32(0.3)                 # one node turns further
+    X0 = X.clone()
+    X0[:, 12:15] = torch.tensor([0.02, -0.01, -0.05], device="cuda")   # field increment
+    X1 = torch.tensor(X1h, device="cuda")
+    T2, dh, change = net.step_targets(X0.contiguous(), X1.contiguous())
+    dh_ref = np.linalg.norm(np.array([0.02, -0.01, -0.05], dtype=np.float32).astype(np.float64))
+    assert dh == pytest.approx(dh_ref, rel=1e-6)
+    d = X1h.astype(np.float64) - Xh.astype(np.float64)
+    np.testing.assert_allclose(T2.cpu().numpy(), np.concatenate([d[:, :3], d[:, 15:16]], 1) / dh_ref,
+                               rtol=1e-4, atol=1e-6)
+    assert change == pytest.approx(np.linalg.norm(d[:, :3], axis=1).max(), rel=1e-5)
+    X0[:, 12:15] = 0.0
+    T3, dh0, _ = net.step_targets(X0.contiguous(), X1.contiguous())
+    assert T3 is None and dh0 == 0.0
