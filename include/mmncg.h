@@ -96,6 +96,17 @@ typedef struct {
                            /* uses algebraic multigrid there), 0 = Jacobi (0).    */
                            /* Needs the hierarchy mm_upload_mesh builds when      */
                            /* n_phi exceeds the dense coarse size; else Jacobi.   */
+    int beta_rule;         /* direction update of Algorithm 3/4 (Sec. 2.1): 0 =   */
+                           /* beta*ZA (default), 1 = beta*FR, 2 = beta*PRP        */
+                           /* (Eqs. FRstar, PRPstar); the descent safeguard is     */
+                           /* the same for all three                               */
+    int poisson_sched;     /* 1: potential tolerance tied to t1 -- an iteration    */
+                           /* whose previous energy decrease dF exceeds 100 times  */
+                           /* the t1 threshold tau_F (1 + |F|) solves to           */
+                           /* poisson_tol * sqrt(dF / threshold) / 10, at most     */
+                           /* poisson_tol_max; otherwise (and on the first         */
+                           /* iteration of a minimisation) to poisson_tol (0)      */
+    double poisson_tol_max;/* loosest scheduled potential tolerance (1e-6)         */
 } mm_params;
 
 /* Counters of one call, in the columns of Table 1 plus the energy. */

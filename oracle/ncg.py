@@ -11,7 +11,9 @@ Steps per field (the order of Algorithm 4):
         d_{j+1} = -y_{j+1} + beta*ZA d_j;
         stop when t1, t2 and t3 all hold.
 
-beta*ZA = (g+ - g).y+ / (g+ - g).d  if y+.g+ > y+.g, else 0.
+beta*ZA = (g+ - g).y+ / (g+ - g).d  if y+.g+ > y+.g, else 0.  The paper's
+other preconditioned rules (Sec. 2.1, Algorithm 3) are selectable:
+beta*FR = g+.y+ / g.y and beta*PRP = (g+ - g).y+ / g.y.
 
 Readings where the paper is silent or garbled (shared exactly with the CUDA
 path):
@@ -34,6 +36,12 @@ path):
     common case, matching evals = 2 nli + n_fields in Tables 1 and 2.
   * Stopping rules t1-t3 use internal units (fem.Units) and the max norm
     over all 3N components.
+  * Potential tolerance (the paper does not state one): poisson_tol for
+    every solve, or with poisson_sched a schedule tied to t1 (see
+    scheduled_tolerance): looser solves while the previous energy decrease
+    is more than 100 times the t1 threshold.
+  * beta*FR / beta*PRP need g_j.y_j of the previous direction; after the
+    safeguard replaced y by g, that is g_j.g_j.
   * Counters: evals (function evaluations), nli (iterations), li (products
     with H in the inner solves), mi (products with K_phi in the loop of the
     Poisson solves; 0 with the direct solver), ls_extra (evaluations spent
@@ -66,6 +74,9 @@ class Params:
     keep_last_term: bool = False
     poisson: str = "direct"        # "direct" or "cg"
     poisson_tol: float = 1e-10
+    beta_rule: str = "ZA"          # "ZA", "FR" or "PRP" (Sec. 2.1, Eqs. FRstar, PRPstar)
+    poisson_sched: bool = False    # potential tolerance tied to t1 (CG potential solve only)
+    poisson_tol_max: float = 1e-6
 
 
 @dataclass
@@ -90,23 +101,63 @@ def beta_za(g_new, g_old, y_new, d_old):
     return 0.0
 
 
-def direction(g_new, g_old, y_new, d_old, counts=None):
-    """d = -y + beta*ZA d_old with the descent safeguard.  With a dict
-    `counts`, the safeguard's branches are tallied: counts["restarts"] when
-    y is replaced by g, counts["steepest"] when d falls back to -g
-    (bookkeeping only)."""
-    beta = beta_za(g_new, g_old, y_new, d_old)
+def beta_fr(g_new, y_new, gy_old):
+    """beta*FR = g_{j+1}.y_{j+1} / g_j.y_j (Eq. FRstar); 0 if g_j.y_j = 0."""
+    return 0.0 if gy_old == 0.0 else float(np.sum(g_new * y_new)) / gy_old
+
+
+def beta_prp(g_new, g_old, y_new, gy_old):
+    """beta*PRP = (g_{j+1} - g_j).y_{j+1} / g_j.y_j (Eq. PRPstar)."""
+    return 0.0 if gy_old == 0.0 else float(np.sum((g_new - g_old) * y_new)) / gy_old
+
+
+def _beta(rule, g_new, g_old, y_new, d_old, gy_old):
+    if rule == "FR":
+        return beta_fr(g_new, y_new, gy_old)
+    if rule == "PRP":
+        return beta_prp(g_new, g_old, y_new, gy_old)
+    return beta_za(g_new, g_old, y_new, d_old)
+
+
+def direction(g_new, g_old, y_new, d_old, counts=None, rule="ZA", gy_old=0.0):
+    """d = -y + beta d_old (beta*ZA, or beta*FR / beta*PRP with gy_old =
+    g_j.y_j of the previous direction) with the descent safeguard: if
+    g.d >= 0, y is replaced by g and beta recomputed; if still g.d >= 0,
+    d = -g.  Returns (d, g_{j+1}.y) with y the vector the direction was built
+    from (g itself after the safeguard), which the next beta*FR / beta*PRP
+    needs.  With a dict `counts`, the safeguard's branches are tallied:
+    counts["restarts"] when y is replaced by g, counts["steepest"] when d
+    falls back to -g (bookkeeping only)."""
+    beta = _beta(rule, g_new, g_old, y_new, d_old, gy_old)
     d = -y_new + beta * d_old
+    gy = float(np.sum(g_new * y_new))
     if float(np.sum(g_new * d)) >= 0.0:
         if counts is not None:
             counts["restarts"] = counts.get("restarts", 0) + 1
-        beta = beta_za(g_new, g_old, g_new, d_old)
+        beta = _beta(rule, g_new, g_old, g_new, d_old, gy_old)
         d = -g_new + beta * d_old
+        gy = float(np.sum(g_new * g_new))
         if float(np.sum(g_new * d)) >= 0.0:
             if counts is not None:
                 counts["steepest"] = counts.get("steepest", 0) + 1
             d = -g_new.copy()
-    return d
+    return d, gy
+
+
+def scheduled_tolerance(p, dF_prev, F0):
+    """Potential tolerance of one iteration with the schedule tied to t1
+    (a reading: the paper leaves the potential tolerance open): while the
+    previous energy decrease dF_prev exceeds 100 times the t1 threshold
+    tau_F (1 + |F|), the solve may stop at poisson_tol sqrt(dF / threshold)
+    / 10 (at most poisson_tol_max) -- the energy error of the variational
+    form is quadratic in the potential error, so it stays far below the
+    decrease the line search resolves; otherwise poisson_tol."""
+    if not p.poisson_sched or dF_prev is None or not dF_prev > 0.0:
+        return p.poisson_tol
+    q = dF_prev / (p.tau_F * (1.0 + abs(F0)))
+    if q <= 100.0:
+        return p.poisson_tol
+    return min(p.poisson_tol_max, max(p.poisson_tol, p.poisson_tol * np.sqrt(q) / 10.0))
 
 
 def cubic_step(f0, g0, a, f1, g1):
@@ -129,8 +180,10 @@ def minimize(P, m0, h, params=None, phi0=None):
     st = {"evals": 0, "nli": 0, "li": 0, "mi": 0, "ls_extra": 0,
           "li2": 0, "li2_first": 0, "restarts": 0, "steepest": 0}
 
+    tol = [p.poisson_tol]
+
     def ev(m, phi_warm):
-        e = evaluate(P, m, h, p.poisson, phi0=phi_warm, tol=p.poisson_tol)
+        e = evaluate(P, m, h, p.poisson, phi0=phi_warm, tol=tol[0])
         st["evals"] += 1
         st["mi"] += e["poisson_steps"]
         return e
@@ -145,9 +198,12 @@ def minimize(P, m0, h, params=None, phi0=None):
     phi = e["phi"]
     y = pre(x, e)
     d = -y
+    gy = float(np.sum(e["g"] * y))
     if float(np.sum(e["g"] * d)) >= 0.0:
         st["steepest"] += 1
         d = -e["g"].copy()
+        gy = float(np.sum(e["g"] * e["g"]))
+    dF_prev = None
     a_prev = 1.0
     status = "max_iter"
     if not np.isfinite(e["F"]):
@@ -156,6 +212,7 @@ def minimize(P, m0, h, params=None, phi0=None):
         status = "converged"
     while status == "max_iter" and st["nli"] < p.max_iter:
         F0 = e["F"]
+        tol[0] = scheduled_tolerance(p, dF_prev, F0)
         dphi0 = float(np.sum(e["g"] * d))
         a_max = p.theta_max / np.max(np.linalg.norm(d, axis=1))
         a_t = min(a_prev, a_max)
@@ -192,6 +249,7 @@ def minimize(P, m0, h, params=None, phi0=None):
                 status = "stalled"
                 break
         st["nli"] += 1
+        dF_prev = F0 - e_b["F"]
         if not np.isfinite(e_b["F"]):
             status = "nonfinite"
             break
@@ -199,7 +257,7 @@ def minimize(P, m0, h, params=None, phi0=None):
         t2 = np.max(np.abs(x - x_b)) < np.sqrt(p.tau_F) * (1.0 + np.max(np.abs(x_b)))
         t3 = np.max(np.abs(e_b["g"])) < p.tau_F ** (1.0 / 3.0) * (1.0 + abs(e_b["F"]))
         y_new = pre(x_b, e_b)
-        d = direction(e_b["g"], e["g"], y_new, d, counts=st)
+        d, gy = direction(e_b["g"], e["g"], y_new, d, counts=st, rule=p.beta_rule, gy_old=gy)
         x, e, a_prev = x_b, e_b, a_b
         if t1 and t2 and t3:
             status = "converged"

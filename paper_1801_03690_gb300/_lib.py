@@ -39,7 +39,8 @@ class mm_params(C.Structure):
                 ("theta_max", C.c_double), ("c1", C.c_double), ("max_backtrack", C.c_int),
                 ("keep_last_term", C.c_int), ("poisson_tol", C.c_double),
                 ("poisson_max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int), ("amg", C.c_int)]
+                ("max_refine", C.c_int), ("amg", C.c_int), ("beta_rule", C.c_int),
+                ("poisson_sched", C.c_int), ("poisson_tol_max", C.c_double)]
 
 
 class mm_stats(C.Structure):

@@ -35,6 +35,9 @@ class Params:
     inner_tol: float = 0.1
     max_refine: int = 64
     amg: int = 0                 # 1 = multigrid-preconditioned FP32 solve
+    beta_rule: int = 0           # 0 = beta*ZA, 1 = beta*FR, 2 = beta*PRP (Sec. 2.1)
+    poisson_sched: int = 0       # 1 = potential tolerance tied to t1
+    poisson_tol_max: float = 1e-6
 
     def to_c(self):
         p = L.mm_params()

@@ -192,6 +192,9 @@ mm::Params to_params(const mm_params* p) {
     q.amg = p->amg;
     q.inner_tol = p->inner_tol;
     q.max_refine = p->max_refine;
+    q.beta_rule = p->beta_rule;
+    q.poisson_sched = p->poisson_sched;
+    q.poisson_tol_max = p->poisson_tol_max;
     return q;
 }
 
@@ -210,6 +213,10 @@ int check_params(mm_ctx* ctx, const mm_params* p) {
         return fail(ctx, MM_ERR_ARG, "inner_tol must be in (0, 1)");
     if (p->precision == 1 && p->max_refine < 1) return fail(ctx, MM_ERR_ARG, "max_refine must be >= 1");
     if (p->amg != 0 && p->amg != 1) return fail(ctx, MM_ERR_ARG, "amg must be 0 or 1");
+    if (p->beta_rule < 0 || p->beta_rule > 2) return fail(ctx, MM_ERR_ARG, "beta_rule must be 0, 1 or 2");
+    if (p->poisson_sched != 0 && p->poisson_sched != 1) return fail(ctx, MM_ERR_ARG, "poisson_sched must be 0 or 1");
+    if (p->poisson_sched && !(p->poisson_tol_max >= p->poisson_tol && p->poisson_tol_max < 1.0))
+        return fail(ctx, MM_ERR_ARG, "poisson_tol_max must be in [poisson_tol, 1)");
     return MM_OK;
 }
 
@@ -895,6 +902,9 @@ void mm_default_params(mm_params* p) {
     p->inner_tol = 0.1;
     p->max_refine = 64;
     p->amg = 0;
+    p->beta_rule = 0;
+    p->poisson_sched = 0;
+    p->poisson_tol_max = 1e-6;
 }
 
 int mm_create(mm_ctx** out, const mm_options* opt) {

@@ -99,6 +99,9 @@ mm::Params conv(const mm_params* p) {
     q.inner_tol = p->inner_tol;
     q.max_refine = p->max_refine;
     q.amg = p->amg;
+    q.beta_rule = p->beta_rule;
+    q.poisson_sched = p->poisson_sched;
+    q.poisson_tol_max = p->poisson_tol_max;
     return q;
 }
 

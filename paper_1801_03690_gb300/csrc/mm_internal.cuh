@@ -56,6 +56,9 @@ struct Params {
     int amg;                 // 1 = aggregation multigrid preconditioner in the FP32 solve
     double inner_tol;        // FP32 solve: relative residual reduction per refinement
     int max_refine;          // FP64 refinement steps per potential solve
+    int beta_rule;           // 0 = beta*ZA, 1 = beta*FR, 2 = beta*PRP
+    int poisson_sched;       // 1 = potential tolerance tied to t1
+    double poisson_tol_max;  // loosest scheduled potential tolerance
 };
 
 // Scalars written back by the kernel (block 0) and read by the host.

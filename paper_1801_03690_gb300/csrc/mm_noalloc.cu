@@ -171,6 +171,9 @@ extern "C" int mm_energy_gradient_noalloc(mm_ctx* ctx, const double* m_dev, cons
     Q.prm.inner_tol = p->inner_tol;
     Q.prm.max_refine = p->max_refine;
     Q.prm.amg = 0;
+    Q.prm.beta_rule = 0;
+    Q.prm.poisson_sched = 0;
+    Q.prm.poisson_tol_max = p->poisson_tol;
     Q.nlev = 0;
     Q.pres32 = Q.pprec32 = Q.pdir32 = Q.pq32 = Q.pdelta32 = nullptr;
 

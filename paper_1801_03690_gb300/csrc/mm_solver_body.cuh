@@ -398,6 +398,8 @@ struct Ctx {
     double h[3];
     SlotScalars sl[MM_NSLOT];
     int y_is_g;
+    double ptol;             // relative residual the potential solves stop at
+    double gy_prev;          // g_j . y_j of the last direction (beta*FR, beta*PRP)
 };
 
 // ---------------------------------------------------------------- phases
@@ -858,7 +860,7 @@ __device__ bool ph_p64_refine(Ctx& C, double& rr) {
 // same direction.  Stops when the FP64 residual meets poisson_tol.
 __device__ bool solve_potential_mixed(Ctx& C, double bb, double rr) {
     const Problem& P = *C.P;
-    const double tol2 = P.prm.poisson_tol * P.prm.poisson_tol * bb;
+    const double tol2 = C.ptol * C.ptol * bb;
     const double upd2 = P.prm.inner_tol * P.prm.inner_tol;
     if (rr < tol2) return true;
     double rz, r32;
@@ -905,7 +907,7 @@ __device__ bool solve_potential(Ctx& C, int s) {
     if (!ph_pinit(C, s, bb, rz, rr)) return false;
     if (bb == 0.0) return ph_pzero(C);
     if (P.prm.precision == 1) return solve_potential_mixed(C, bb, rr);
-    const double tol2 = P.prm.poisson_tol * P.prm.poisson_tol * bb;
+    const double tol2 = C.ptol * C.ptol * bb;
     double beta = 0.0;
     long long k = 0;
     while (rr >= tol2 && k < P.prm.poisson_max_iter) {
@@ -1247,12 +1249,24 @@ __device__ __forceinline__ double beta_za(double y_gn, double y_go, double dg_y,
     return 0.0;
 }
 
+// The direction update of Algorithm 3/4 with y the preconditioned new
+// gradient: beta*ZA (restarted Hestenes-Stiefel), beta*FR = g+.y+ / g.y
+// (Eq. FRstar), beta*PRP = (g+ - g).y+ / g.y (Eq. PRPstar), g.y = gy_prev
+// of the last direction (0 gives beta = 0).
+__device__ __forceinline__ double beta_rule(int rule, double y_gn, double y_go, double dg_y, double dg_d,
+                                            double gy_prev) {
+    if (rule == 1) return (gy_prev == 0.0) ? 0.0 : y_gn / gy_prev;
+    if (rule == 2) return (gy_prev == 0.0) ? 0.0 : dg_y / gy_prev;
+    return beta_za(y_gn, y_go, dg_y, dg_d);
+}
+
 // New direction with beta*ZA and the descent safeguard; returns g.d.
 __device__ bool direction(Ctx& C, int a, int c, bool initial, double& dmax, double& gd) {
     double dots[8];
     if (!ph_dir_dots(C, a, c, dots)) return false;
     const double y_gn = dots[0], y_go = dots[1], dg_y = dots[2], dg_d = dots[3];
     const double gn_d = dots[4], gn_gn = dots[5], gn_go = dots[6], dg_gn = dots[7];
+    const int rule = C.P->prm.beta_rule;
     int kind = 1;
     double beta = 0.0;
     if (initial) {
@@ -1263,10 +1277,10 @@ __device__ bool direction(Ctx& C, int a, int c, bool initial, double& dmax, doub
             C.steepest++;
         }
     } else {
-        beta = beta_za(y_gn, y_go, dg_y, dg_d);
+        beta = beta_rule(rule, y_gn, y_go, dg_y, dg_d, C.gy_prev);
         gd = -y_gn + beta * gn_d;
         if (gd >= 0.0) {
-            beta = beta_za(gn_gn, gn_go, dg_gn, dg_d);
+            beta = beta_rule(rule, gn_gn, gn_go, dg_gn, dg_d, C.gy_prev);
             kind = 2;
             gd = -gn_gn + beta * gn_d;
             C.restarts++;
@@ -1278,6 +1292,7 @@ __device__ bool direction(Ctx& C, int a, int c, bool initial, double& dmax, doub
             }
         }
     }
+    C.gy_prev = (kind == 1) ? y_gn : gn_gn;     // g.y of the direction built (y = g after the safeguard)
     return ph_dir_write(C, a, kind, beta, dmax);
 }
 
@@ -1308,8 +1323,18 @@ __device__ int minimize(Ctx& C, int& cur) {
     else if (C.sl[c].gmax == 0.0) status = ST_OK;
     const double sq_tau = sqrt(prm.tau_F);
     const double cb_tau = cbrt(prm.tau_F);
+    double dF_prev = -1.0;                      // last accepted decrease (none yet)
     while (status == ST_RUNNING && C.nli < prm.max_iter) {
         const double F0 = C.sl[c].F;
+        // potential tolerance of this iteration's evaluations (poisson_sched):
+        // loosened while the last decrease is far above the t1 threshold, so
+        // that the energy error (quadratic in the potential error) stays far
+        // below the decrease the line search resolves
+        C.ptol = prm.poisson_tol;
+        if (prm.poisson_sched && dF_prev > 0.0) {
+            const double q = dF_prev / (prm.tau_F * (1.0 + fabs(F0)));
+            if (q > 100.0) C.ptol = fmin(prm.poisson_tol_max, fmax(prm.poisson_tol, prm.poisson_tol * sqrt(q) / 10.0));
+        }
         const double dphi0 = gd;
         const double a_max = prm.theta_max / dmax;
         const double a_t = fmin(a_prev, a_max);
@@ -1350,6 +1375,7 @@ __device__ int minimize(Ctx& C, int& cur) {
         }
         C.nli++;
         const SlotScalars& S = C.sl[b];
+        dF_prev = F0 - S.F;
         if (!isfinite(S.F)) {
             status = ST_NONFINITE;
             break;
@@ -1387,6 +1413,8 @@ __device__ __forceinline__ void solver_body(const Problem& P, int nb, int rank) 
     C.evals = C.nli = C.li = C.mi = C.ls_extra = C.mr = 0;
     C.li2 = C.li2_first = C.restarts = C.steepest = 0;
     C.y_is_g = 0;
+    C.ptol = P.prm.poisson_tol;
+    C.gy_prev = 0.0;
     int cur = P.state->cur;
     C.h[0] = P.state->h[0];
     C.h[1] = P.state->h[1];

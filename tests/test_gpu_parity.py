@@ -320,3 +320,55 @@ def test_rare_branches_fire_and_match_oracle(lib, case):
     assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
     assert np.abs(mag.get_magnetization()[P.mag_nodes] - r.m).max() < 1e-5
     mag.close()
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+def test_beta_rules_match_oracle(lib, rule):
+    """beta*FR (1) and beta*PRP (2) of Sec. 2.1 / Algorithm 3 selected in
+    place of beta*ZA: the GPU minimisation follows the oracle's path with
+    the same rule and reaches the same minimum."""
+    Magnet, Params = lib
+    wl = _hard(n_mag=5)
+    mag, P = _setup(lib, wl)
+    b = np.array([0.2, 0.0, -1.0])
+    mag.set_magnetization(wl.m0)
+    mag.set_field(b)
+    st = mag.minimize(Params(jmax=4, beta_rule=rule, **TIGHT))
+    r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=4, beta_rule={1: "FR", 2: "PRP"}[rule]))
+    assert st["status"] == "ok" and r.status == "converged"
+    _same_path(st, r)
+    assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+    assert np.abs(mag.get_magnetization()[P.mag_nodes] - r.m).max() < 1e-5
+    mag.close()
+
+
+@pytest.mark.parametrize("prec,amg", [(0, 0), (1, 1)])
+def test_poisson_schedule_keeps_the_minimum(lib, prec, amg):
+    """The potential tolerance tied to t1 (poisson_sched): the same minimum
+    as the oracle's (energy 1e-8, max nodal |dm| 1e-5) and as the GPU
+    without the schedule, with fewer potential steps; the plain FP64 form
+    along the same path as the oracle with the same schedule."""
+    Magnet, Params = lib
+    wl = synth.hard_cube(n_mag=16)
+    mag, P = _setup(lib, wl)
+    b = wl.fields[3]
+    base = dict(jmax=4, precision=prec, amg=amg, inner_tol=1e-3 if amg else 0.1)
+    out = []
+    for sched in (0, 1):
+        mag.set_magnetization(wl.m0)
+        mag.set_field(b)
+        out.append((mag.minimize(Params(poisson_sched=sched, **base)), mag.get_magnetization()[P.mag_nodes]))
+    (s0, m0), (s1, m1) = out
+    r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=4, poisson="cg", poisson_sched=True))
+    assert s1["status"] == "ok" and r.status == "converged"
+    assert s1["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+    assert np.abs(m1 - r.m).max() < 1e-5
+    assert s1["F"] == pytest.approx(s0["F"], rel=1e-8)
+    assert np.abs(m1 - m0).max() < 1e-5
+    assert s1["mi"] < s0["mi"]
+    if prec == 0:
+        for k in ("nli", "evals", "li", "ls_extra"):
+            assert s1[k] == r.stats[k], (k, s1[k], r.stats[k])
+    mag.close()

@@ -31,14 +31,17 @@ def test_direction_safeguard():
     d_old = np.array([[0.0, 10.0, 0.0]])
     # y pointing against g: -y is ascent, beta = 0 -> replaced by y = g
     y_new = np.array([[0.0, -1.0, 0.0]])
-    d = ncg.direction(g_new, g_old, y_new, d_old)
+    d, gy = ncg.direction(g_new, g_old, y_new, d_old)
     assert float(np.sum(g_new * d)) < 0
+    assert gy == pytest.approx(1.0)                      # y was replaced by g
     # a regular case keeps d = -y + beta d_old
     y_ok = np.array([[0.0, 0.5, 0.0]])
     d_prev = np.array([[-1.0, 0.0, 0.0]])
     beta = ncg.beta_za(g_new, g_old, y_ok, d_prev)
     assert beta == pytest.approx(0.5)
-    np.testing.assert_allclose(ncg.direction(g_new, g_old, y_ok, d_prev), [[-0.5, -0.5, 0.0]])
+    d, gy = ncg.direction(g_new, g_old, y_ok, d_prev)
+    np.testing.assert_allclose(d, [[-0.5, -0.5, 0.0]])
+    assert gy == pytest.approx(0.5)
 
 
 def test_cubic_step_exact_for_cubics():
@@ -172,3 +175,65 @@ def test_stoner_wohlfarth_curve():
     res = curve.demag_curve(P, fields, m0, ncg.Params(jmax=4))
     assert abs(res["Hc_T"] - bsw) <= 0.01 * bsw
     assert all(rec["status"] == "converged" for rec in res["records"])
+
+
+@pytest.mark.parametrize("rule", ["ZA", "FR", "PRP"])
+def test_preconditioned_rules_are_linear_pcg_on_a_quadratic(rule):
+    """On F = 1/2 x^T A x - b^T x with exact line searches and y = M^-1 g
+    (M = diag A), beta*ZA, beta*FR and beta*PRP (Sec. 2.1, Algorithm 3) all
+    reproduce preconditioned linear CG: the directions are A-conjugate and
+    the minimiser is reached in n steps (in exact arithmetic)."""
+    rng = np.random.default_rng(5)
+    n = 12
+    Q = rng.standard_normal((n, n))
+    A = Q @ Q.T + n * np.eye(n)
+    b = rng.standard_normal(n)
+    Minv = 1.0 / np.diag(A)
+    x = np.zeros(n)
+    g = A @ x - b
+    y = Minv * g
+    d = -y
+    gy = float(g @ y)
+    dirs = []
+    for _ in range(n):
+        dirs.append(d.copy())
+        a = -float(g @ d) / float(d @ A @ d)            # exact line search
+        x = x + a * d
+        g_new = A @ x - b
+        if np.linalg.norm(g_new) < 1e-12 * np.linalg.norm(b):
+            break
+        y_new = Minv * g_new
+        dn, gy = ncg.direction(g_new.reshape(-1, 3), g.reshape(-1, 3), y_new.reshape(-1, 3),
+                               d.reshape(-1, 3), rule=rule, gy_old=gy)
+        d = dn.reshape(-1)
+        g = g_new
+    np.testing.assert_allclose(A @ x, b, rtol=0, atol=1e-9 * np.abs(b).max())
+    D = np.array(dirs)
+    C = D @ A @ D.T
+    off = C - np.diag(np.diag(C))
+    assert np.abs(off).max() <= 1e-8 * np.abs(np.diag(C)).max()
+
+
+def test_tolerance_schedule_values():
+    p = ncg.Params(poisson_sched=True, tau_F=1e-10, poisson_tol=1e-10, poisson_tol_max=1e-6)
+    F0 = 99.0                                             # threshold tau_F (1 + |F|) = 1e-8
+    assert ncg.scheduled_tolerance(p, None, F0) == 1e-10            # first iteration
+    assert ncg.scheduled_tolerance(p, 1e-6, F0) == 1e-10            # q = 100: not loosened
+    assert ncg.scheduled_tolerance(p, 1e-2, F0) == pytest.approx(1e-10 * 1e3 / 10)   # q = 1e6
+    assert ncg.scheduled_tolerance(p, 1e8, F0) == 1e-6               # capped
+    assert ncg.scheduled_tolerance(ncg.Params(), 1e8, F0) == 1e-10   # schedule off
+
+
+def test_tolerance_schedule_keeps_the_minimum():
+    """The scheduled potential tolerance reaches the same minimum (energy
+    1e-9 relative, m 1e-6) with fewer potential CG steps."""
+    wl = synth.small_cube(n_mag=5, h=2e-9, jitter=0.05, seed=3)
+    P = fem.assemble_workload(wl)
+    m0 = energy.normalize(wl.m0[P.mag_nodes])
+    h = P.units.field_int(np.array([0.02, 0.0, 0.05]))
+    r0 = ncg.minimize(P, m0, h, ncg.Params(jmax=4, poisson="cg"))
+    r1 = ncg.minimize(P, m0, h, ncg.Params(jmax=4, poisson="cg", poisson_sched=True))
+    assert r0.status == "converged" and r1.status == "converged"
+    assert r1.F == pytest.approx(r0.F, rel=1e-9)
+    assert np.abs(r1.m - r0.m).max() < 1e-6
+    assert r1.stats["mi"] < r0.stats["mi"]
