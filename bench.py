@@ -355,12 +355,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-curve", action="store_true", help="skip the full hard-cube curves")
-    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling"],
+    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling", "sp3"],
                     help="steps: the timed field steps (default line); curve: full demagnetisation "
                          "curves of the plain FP64, precision and precision + learned forms; "
                          "batch: the batched platelet workload; scaling: field steps of the hard "
                          "cube at several resolutions")
     ap.add_argument("--n-platelets", type=int, default=64)
+    ap.add_argument("--sp3-edges", default="8.2,8.4,8.6,8.8", help="sp3 mode: cube edges in exchange lengths")
+    ap.add_argument("--sp3-n", type=int, default=24, help="sp3 mode: voxels per cube edge")
+    ap.add_argument("--sp3-jmax", type=int, default=12, help="sp3 mode: j_max (Table 3's best: 12)")
     ap.add_argument("--forms", default="plain_fp64,precision,precision_multigrid,precision_learned")
     ap.add_argument("--theta-max", type=float, default=0.1,
                     help="curve mode: line-search cap on the largest nodal step (the paper's reading: 0.1)")
@@ -416,6 +419,8 @@ def main():
         return batch_mode(args, rank, local_rank)
     if args.mode == "scaling":
         return scaling_mode(args, rank, local_rank)
+    if args.mode == "sp3":
+        return sp3_mode(args, rank, local_rank)
 
     t0 = time.perf_counter()
     wl = workload(args.workload)
@@ -687,6 +692,48 @@ def curve_mode(args, rank, local_rank):
         print(json.dumps({"mode": "curve", "workload": wl.name, "sizes": sz, "n_fields": len(fields),
                           "forms": out}))
     mag.close()
+    return 0
+
+
+def sp3_mode(args, rank, local_rank):
+    """muMAG standard problem 3 (Sec. 3.3): flower (from saturation) and
+    vortex (from a sharp two-domain state) relaxed at zero field with
+    tau_F = 1e-12 for cube edges L around the single-domain limit; reduced
+    energies e = E / (Km L^3) and the edge where they cross, by linear
+    interpolation of e_flower - e_vortex."""
+    import torch
+    import synth
+    from paper_1801_03690_gb300 import Magnet, Params
+    Ls = [float(x) for x in args.sp3_edges.split(",")]
+    prm = Params(tau_F=1e-12, jmax=args.sp3_jmax, poisson_tol=1e-12, max_iter=100000)
+    rows = []
+    for L in Ls:
+        row = {"L_lex": L}
+        for start in ("flower", "vortex"):
+            wl = synth.sp3_cube(L, n_mag=args.sp3_n, start=start)
+            mag = Magnet(device=local_rank)
+            mag.upload_workload(wl)
+            mag.set_magnetization(wl.m0)
+            t0 = time.perf_counter()
+            st = mag.minimize(prm)
+            dt = time.perf_counter() - t0
+            km, Lm = wl.meta["Km"], wl.meta["L"]
+            row[start] = {"e": st["F"] / (km * Lm ** 3), "terms": [t / (km * Lm ** 3) for t in st["terms"]],
+                          "M": st["M"], "status": st["status"], "nli": st["nli"], "evals": st["evals"],
+                          "li": st["li"], "mi": st["mi"], "seconds": dt}
+            mag.close()
+        row["de"] = row["flower"]["e"] - row["vortex"]["e"]
+        rows.append(row)
+        if rank == 0:
+            print(json.dumps(row), flush=True)
+    cross = None
+    for a, b in zip(rows[:-1], rows[1:]):
+        if a["de"] * b["de"] < 0:
+            cross = a["L_lex"] + a["de"] / (a["de"] - b["de"]) * (b["L_lex"] - a["L_lex"])
+            break
+    if rank == 0:
+        print(json.dumps({"mode": "sp3", "n_mag": args.sp3_n, "jmax": args.sp3_jmax, "crossover_L_lex": cross,
+                          "paper": 8.52, "rows": rows}))
     return 0
 
 

@@ -108,6 +108,7 @@ EXPORTS = {
                                   C.POINTER(C.c_float)]),
     "mm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
                                     C.POINTER(C.c_float)]),
+    "mm_mlp_set_tensor_path": (C.c_int, [C.c_void_p, C.c_int]),
     "mm_mlp_fit_input_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "mm_mlp_get_input_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mm_mlp_fit_target_scales": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,

@@ -415,6 +415,12 @@ class MLP:
         if rc:
             raise MMError(rc, "mm_mlp_set_input_norm")
 
+    def set_tensor_path(self, path):
+        """0: tcgen05 forward pass (default); 1: mma.sync (comparison)."""
+        rc = self._lib.mm_mlp_set_tensor_path(self._h, int(path))
+        if rc:
+            raise MMError(rc, "mm_mlp_set_tensor_path")
+
     def fit_input_norm(self, X):
         """Input standardisation from the data X [n, 16] (float32, device)."""
         assert X.is_cuda and X.is_contiguous() and X.shape[1] == 16

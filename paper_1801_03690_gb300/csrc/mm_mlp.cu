@@ -4,8 +4,11 @@
 // of the scalar potential.  Plain NCG then runs to t1-t3 from the corrected
 // state, so the network only changes where the minimiser starts.
 //
-// All products run on the tensor cores with mma.sync m16n8k16 (BF16
-// operands, FP32 accumulation):
+// The forward pass runs on the 5th-generation tensor cores (tcgen05.mma,
+// accumulators in tensor memory: mm_mlp_tc.cuh); the same network on the
+// warp-level mma.sync m16n8k16 path (BF16 operands, FP32 accumulation) is
+// kept as a measured comparison (mm_mlp_set_tensor_path), and the backward
+// kernels use it:
 //   k_mlp_forward   persistent; the weights (BF16, [out][in]) live in shared
 //                   memory; inputs are standardised in FP32 (the network's
 //                   own mean and 1/std) before the BF16 conversion, then each
@@ -609,6 +612,8 @@ __global__ void k_scale_targets(long long n, const float* __restrict__ T, float 
     Tn[i * NOUT + 3] = T[i * NOUT + 3] / sp;
 }
 
+#include "mm_mlp_tc.cuh"
+
 struct mm_mlp {
     int device = 0;
     int nsm = 0;
@@ -632,6 +637,8 @@ struct mm_mlp {
     float *F = nullptr, *FY = nullptr;
     mm::Problem* d_prob = nullptr;
     unsigned* d_max = nullptr;
+    int* d_err = nullptr;         // set by a tensor-core wait that ran out
+    int path = 0;                 // 0: tcgen05 forward pass, 1: mma.sync (comparison)
 };
 
 namespace {
@@ -680,6 +687,14 @@ int ensure(mm_mlp* M, long long n) {
 }
 
 int launch_forward(mm_mlp* M, const float* X, long long n, float* Y, bool train) {
+    if (M->path == 0) {
+        const int grid = std::max(1, std::min((int)((n + tc::TM - 1) / tc::TM), M->nsm));
+        tc::k_mlp_forward_tc<<<grid, tc::TM, sizeof(tc::Smem), M->stream>>>(
+            n, X, M->wb, M->p, M->norm, Y, train ? M->A1 : nullptr, train ? M->A2 : nullptr,
+            train ? M->A3 : nullptr, train ? M->X0 : nullptr, M->d_err);
+        MK(cudaGetLastError());
+        return MM_OK;
+    }
     const int grid = std::max(1, std::min((int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK), 2 * M->nsm));
     k_mlp_forward<<<grid, WARPS * 32, fwd_smem(), M->stream>>>(n, X, M->wb, M->p, M->norm, Y, train ? M->A1 : nullptr,
                                                                train ? M->A2 : nullptr, train ? M->A3 : nullptr,
@@ -716,11 +731,29 @@ int gradient(mm_mlp* M, const float* X, const float* T, long long n) {
     return MM_OK;
 }
 
+// MM_ERR_DEVICE_TIMEOUT if a tensor-core wait of the last launches ran out
+// (the flag is cleared); call after synchronising the stream.
+int check_err(mm_mlp* M) {
+    int e = 0;
+    MK(cudaMemcpy(&e, M->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) return MM_OK;
+    MK(cudaMemset(M->d_err, 0, sizeof(int)));
+    return MM_ERR_DEVICE_TIMEOUT;
+}
+
 }  // namespace
 
 extern "C" {
 
 int64_t mm_mlp_param_count(void) { return NPARAM; }
+
+int mm_mlp_set_tensor_path(mm_mlp* M, int path) {
+    if (!M || (path != 0 && path != 1)) return MM_ERR_ARG;
+    MK(cudaSetDevice(M->device));
+    MK(cudaStreamSynchronize(M->stream));
+    M->path = path;
+    return MM_OK;
+}
 
 int mm_mlp_create(mm_mlp** out, int device, uint64_t seed) {
     if (!out) return MM_ERR_ARG;
@@ -741,8 +774,9 @@ int mm_mlp_create(mm_mlp** out, int device, uint64_t seed) {
         cudaMalloc(&M->av, NPARAM * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&M->loss, sizeof(float)) != cudaSuccess || cudaMalloc(&M->d_prob, sizeof(mm::Problem)) != cudaSuccess ||
         cudaMalloc(&M->norm, 2 * NIN * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&M->d_max, sizeof(unsigned)) != cudaSuccess)
+        cudaMalloc(&M->d_max, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&M->d_err, sizeof(int)) != cudaSuccess)
         return bail(MM_ERR_OOM);
+    if (cudaMemset(M->d_err, 0, sizeof(int)) != cudaSuccess) return bail(MM_ERR_CUDA);
     {
         float id[2 * NIN];
         for (int i = 0; i < NIN; ++i) {
@@ -756,7 +790,9 @@ int mm_mlp_create(mm_mlp** out, int device, uint64_t seed) {
         cudaFuncSetAttribute(k_mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem()) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem()) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(tc::Smem)) != cudaSuccess)
         return bail(MM_ERR_CUDA);
     // He-uniform initialisation (host RNG, seeded), zero biases
     std::vector<float> h(NPARAM, 0.0f);
@@ -780,7 +816,7 @@ void mm_mlp_destroy(mm_mlp* M) {
     for (void* q : {(void*)M->p, (void*)M->norm, (void*)M->wb, (void*)M->g, (void*)M->am, (void*)M->av, (void*)M->loss,
                     (void*)M->X0, (void*)M->A1, (void*)M->A2, (void*)M->A3, (void*)M->DZ1, (void*)M->DZ2,
                     (void*)M->DZ3, (void*)M->DZ4, (void*)M->Yb, (void*)M->part, (void*)M->F, (void*)M->FY,
-                    (void*)M->d_prob, (void*)M->d_max})
+                    (void*)M->d_prob, (void*)M->d_max, (void*)M->d_err})
         if (q) cudaFree(q);
     if (M->stream) cudaStreamDestroy(M->stream);
     delete M;
@@ -826,7 +862,7 @@ int mm_mlp_forward(mm_mlp* M, const float* X_dev, int64_t n, float* Y_dev) {
     int rc = launch_forward(M, X_dev, n, Y_dev, false);
     if (rc) return rc;
     MK(cudaStreamSynchronize(M->stream));
-    return MM_OK;
+    return check_err(M);
 }
 
 int mm_mlp_gradient(mm_mlp* M, const float* X_dev, const float* T_dev, int64_t n, float* grad_host,
@@ -838,6 +874,7 @@ int mm_mlp_gradient(mm_mlp* M, const float* X_dev, const float* T_dev, int64_t n
     k_mlp_loss<<<1, 256, 0, M->stream>>>(n, M->Yb, T_dev, M->loss);
     MK(cudaGetLastError());
     MK(cudaStreamSynchronize(M->stream));
+    if ((rc = check_err(M))) return rc;
     if (grad_host) MK(cudaMemcpy(grad_host, M->g, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
     if (loss_out) MK(cudaMemcpy(loss_out, M->loss, sizeof(float), cudaMemcpyDeviceToHost));
     return MM_OK;
@@ -859,6 +896,7 @@ int mm_mlp_train_step(mm_mlp* M, const float* X_dev, const float* T_dev, int64_t
         MK(cudaGetLastError());
         MK(cudaMemcpyAsync(loss_out, M->loss, sizeof(float), cudaMemcpyDeviceToHost, M->stream));
         MK(cudaStreamSynchronize(M->stream));
+        if ((rc = check_err(M))) return rc;
     }
     return MM_OK;
 }
@@ -1030,6 +1068,7 @@ int mm_warmstart_apply(mm_ctx* ctx, mm_mlp* M, const double mu0h_next[3], double
     if (rc) return rc;
     if ((rc = launch_forward(M, M->F, v.nm, M->FY, false))) return rc;
     MK(cudaStreamSynchronize(M->stream));
+    if ((rc = check_err(M))) return mm::ctx_fail(ctx, rc, "a tensor-core wait of the network ran out");
     mm::DevState hs;
     MK(cudaMemcpy(&hs, v.d_state, sizeof(mm::DevState), cudaMemcpyDeviceToHost));
     const double s = 1.0 / (4e-7 * 3.14159265358979323846 * v.Mref);

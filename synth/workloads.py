@@ -201,6 +201,28 @@ def large_polycrystal(n_mag=149, edge=250e-9, box_factor=2.0, ratio=1.06, n_grai
                           "graded_ratio": ratio, "n_mag": n_mag})
 
 
+def sp3_cube(L_lex, n_mag=24, box_factor=4.0, ratio=1.15, Ms=8.0e5, A=1.3e-11, start="flower"):
+    """The cube of the muMAG standard problem 3 (Sec. 3.3): edge L = L_lex
+    exchange lengths l_ex = sqrt(A / Km), Km = mu0 Ms^2 / 2, uniaxial
+    anisotropy K = 0.1 Km along z, n_mag^3 voxels (h = L / n_mag; 24 voxels
+    give h = 0.35 l_ex at L = 8.4 l_ex), in an air box of box_factor x L
+    graded by `ratio` per cell, zero applied field.  start = "flower": the
+    saturated state m = +z; start = "vortex": two domains m = +z (x < 0) and
+    m = -z (x > 0) with a sharp transition."""
+    km = 0.5 * MU0 * Ms ** 2
+    lex = np.sqrt(A / km)
+    L = L_lex * lex
+    mesh = graded_cube_in_box(n_mag, L, box_factor, ratio)
+    mats = _material_table([(0, 0, 0, 0, 0, 1), (Ms, A, 0.1 * km, 0.0, 0.0, 1.0)])
+    m0 = np.tile([0.0, 0.0, 1.0], (mesh.n_nodes, 1))
+    if start == "vortex":
+        m0[mesh.xyz[:, 0] > 0.0, 2] = -1.0
+    elif start != "flower":
+        raise ValueError(start)
+    return Workload(name=f"sp3_{L_lex:.2f}lex_{start}", mesh=mesh, materials=mats, fields=np.zeros((1, 3)), m0=m0,
+                    meta={"L": L, "lex": lex, "Km": km, "n_mag": n_mag, "h_lex": L_lex / n_mag})
+
+
 def _graded_axis(half_mag, h, half_box, ratio):
     """Coordinates covering [-half_box, half_box]: uniform spacing h over
     [-half_mag, half_mag], then spacing growing by `ratio` per cell outward."""

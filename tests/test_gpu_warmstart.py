@@ -155,3 +155,43 @@ def test_library_training_statistics_match_their_definitions():
     X0[:, 12:15] = 0.0
     T3, dh0, _ = net.step_targets(X0.contiguous(), X1.contiguous())
     assert T3 is None and dh0 == 0.0
+
+
+def _deviation_stats(Y, Yr):
+    d = np.abs(Y - Yr) / np.abs(Yr).max()
+    return float(d.max()), float(np.quantile(d, 0.5)), float(np.quantile(d, 0.9))
+
+
+@pytest.mark.parametrize("n", [128, 301, 20000])
+def test_tcgen05_forward_matches_reference_and_mma_sync(n):
+    """The tcgen05 forward pass (default) against the oracle's network and
+    against the warp-level mma.sync path, on full tiles, a ragged tail and
+    many tiles.  All three round at the same points (BF16 inputs, weights,
+    hidden activations); they differ in FP32 (GPU) vs FP64 (oracle)
+    accumulation order, which moves an output by ~1e-6 of the largest and,
+    where a hidden activation lies within that of a BF16 rounding boundary,
+    flips it by one BF16 unit (2^-8 relative): the median deviation must be
+    at rounding level and the largest within a few BF16 units."""
+    import torch
+    from paper_1801_03690_gb300 import MLP
+    net = MLP(seed=4)
+    p = net.get_params()
+    rng = np.random.default_rng(9)
+    for off in (16 * 128, 16 * 128 + 128 + 128 * 128, 16 * 128 + 2 * (128 + 128 * 128)):
+        p[off:off + 128] = rng.normal(size=128) * 0.1                  # nonzero biases
+    net.set_params(p)
+    X = rng.normal(size=(n, 16)).astype(np.float32)
+    Xd = torch.tensor(X, device="cuda")
+    Y_tc = net.forward(Xd).cpu().numpy()
+    net.set_tensor_path(1)
+    Y_ms = net.forward(Xd).cpu().numpy()
+    net.set_tensor_path(0)
+    Yr, _ = omlp.forward(_params_list(p), X.astype(np.float64), round_bf16=True)
+    for name, Y in (("tcgen05", Y_tc), ("mma.sync", Y_ms)):
+        mx, med, q90 = _deviation_stats(Y, Yr)
+        print(f"{name} vs oracle, n={n}: max {mx:.2e} median {med:.2e} q90 {q90:.2e} (of the largest output)")
+        assert mx <= 1e-2 and med <= 1e-5, (name, mx, med)
+    mx, med, q90 = _deviation_stats(Y_tc, Y_ms)
+    print(f"tcgen05 vs mma.sync, n={n}: max {mx:.2e} median {med:.2e} q90 {q90:.2e}")
+    assert mx <= 1e-2 and med <= 1e-5
+    assert np.isfinite(Y_tc).all()
