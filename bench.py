@@ -351,6 +351,8 @@ def main():
     ap.add_argument("--workload", default="large_polycrystal", choices=WORKLOADS)
     ap.add_argument("--fp64-steps", type=int, default=8,
                     help="timed field steps of the plain FP64 comparison (a prefix of the timed steps)")
+    ap.add_argument("--fp64-slice", type=int, default=200,
+                    help="curve mode: iterations of the switching step timed in plain FP64 for the extrapolation")
     ap.add_argument("--jacobi", action="store_true", help="also time the Jacobi-preconditioned precision form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -615,12 +617,20 @@ def main():
 
 
 def curve_mode(args, rank, local_rank):
-    """Full demagnetisation curves of one workload in four forms: plain FP64,
-    the precision form with the Jacobi and with the multigrid potential
-    preconditioner, and the multigrid precision form with the learned warm
-    start (network trained on the curve of a coarser mesh of the same
-    recipe).  Reports wall time, NCG iterations and coercive field."""
+    """Full demagnetisation curves of one workload, in the forms listed by
+    --forms: plain_fp64, precision (Jacobi), precision_multigrid, and
+    precision_learned (the multigrid precision form with the learned warm
+    start, the network trained on the method's own trajectories of the
+    hard-cube and polycrystal recipes at reduced resolution, i.e. of other
+    meshes).  plain_fp64_extrapolated: plain FP64 timed on a slice of the
+    curve -- the warm-up-free reversible field steps after the first and the
+    first --fp64-slice iterations of the switching step, from the multigrid
+    form's states there -- and extrapolated to the whole curve with the
+    multigrid form's per-step iteration counts (both forms take the same
+    iterations; labelled extrapolated).  Reports wall time, NCG iterations,
+    potential steps and coercive field (mm_coercive_field)."""
     import torch
+    import synth
     from paper_1801_03690_gb300 import Magnet, Params, MLP, warmstart, coercive_field
     wl = workload(args.workload)
     fields = wl.fields
@@ -628,69 +638,102 @@ def curve_mode(args, rank, local_rank):
     mag.upload_workload(wl)
     sz = mag.sizes()
     out = {}
-
     forms = args.forms.split(",")
+    states = {}
 
-    def run(name, prm, net=None, scales=None):
+    def run(name, prm, net=None, scales=None, keep_states=False):
         if name not in forms:
             return
         mag.set_magnetization(wl.m0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sts = []
+        sts, kms = [], []
         for k, b in enumerate(fields):
+            if keep_states:
+                states[k] = mag.get_magnetization()
             if net is not None and k > 0:
                 warmstart.warmstart_apply(mag, net, b, scales[0], scales[1], args.max_change)
             mag.set_field(b)
             sts.append(mag.minimize(prm))
+            kms.append(mag.last_kernel_ms())
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         M = np.array([s["M"] for s in sts])
-        out[name] = {"wall_s": wall, "nli": int(sum(s["nli"] for s in sts)),
+        out[name] = {"wall_s": wall, "kernel_s": sum(kms) / 1e3, "nli": int(sum(s["nli"] for s in sts)),
                      "evals": int(sum(s["evals"] for s in sts)), "mi": int(sum(s["mi"] for s in sts)),
                      "Hc_T": coercive_field(fields, M),
                      "statuses": sorted(set(s["status"] for s in sts)),
-                     "nli_per_step": [int(s["nli"]) for s in sts], "Mz": M[:, 2].tolist()}
+                     "nli_per_step": [int(s["nli"]) for s in sts], "kernel_ms_per_step": kms,
+                     "Mz": M[:, 2].tolist()}
 
     run("plain_fp64", Params(precision=0, theta_max=args.theta_max))
     run("precision", Params(precision=1, theta_max=args.theta_max))
-    run("precision_multigrid", Params(precision=1, amg=1, inner_tol=1e-3, theta_max=args.theta_max))
-    # learned warm start: train on the curve of the same recipe at half the resolution
-    if "precision_learned" not in forms:
-        if rank == 0:
-            print(json.dumps({"mode": "curve", "workload": wl.name, "sizes": sz, "forms": out}))
-        return 0
-    t0 = time.perf_counter()
-    import synth
-    coarse = synth.hard_cube(n_mag=max(8, wl.meta.get("n_mag", 48) // 2), seed=12,
-                             n_fields=len(fields)) if args.workload == "hard_cube" else None
-    if coarse is None:
-        coarse = synth.hard_cube(n_mag=12, seed=12, n_fields=len(fields))
-    tm = Magnet(device=local_rank)
-    tm.upload_workload(coarse)
-    net = MLP(device=local_rank, seed=11)
-    X, T, _ = warmstart.collect(tm, net, coarse.m0, coarse.fields, tm.sizes()["n_mag"],
-                                Params(precision=1, amg=1, inner_tol=1e-3))
-    tm.close()
-    s_m, s_p, losses = warmstart.train(net, X, T, steps=1500, batch=16384, lr=2e-3, log_every=500)
-    train_s = time.perf_counter() - t0
-    run("precision_learned", Params(precision=1, amg=1, inner_tol=1e-3, theta_max=args.theta_max), net=net,
-        scales=(s_m, s_p))
-    ref = out.get("plain_fp64") or out.get("precision")
+    mg = Params(precision=1, amg=1, inner_tol=1e-3, theta_max=args.theta_max)
+    run("precision_multigrid", mg, keep_states="plain_fp64_extrapolated" in forms)
+    if "plain_fp64_extrapolated" in forms and "precision_multigrid" in out:
+        ref = out["precision_multigrid"]
+        nli = np.array(ref["nli_per_step"])
+        ksw = int(np.argmax(nli))                       # the switching step
+        fp = Params(precision=0, theta_max=args.theta_max)
+        rev = [k for k in range(1, len(fields)) if k != ksw][:args.fp64_steps]
+        t_rev, n_rev = 0.0, 0
+        for k in rev:
+            mag.set_magnetization(states[k])
+            mag.set_field(fields[k - 1])
+            mag.minimize(fp)                            # the previous minimum in this form (untimed)
+            mag.set_field(fields[k])
+            st = mag.minimize(fp)
+            t_rev += mag.last_kernel_ms() / 1e3
+            n_rev += st["nli"]
+        mag.set_magnetization(states[ksw])
+        mag.set_field(fields[ksw - 1])
+        mag.minimize(fp)
+        mag.set_field(fields[ksw])
+        st = mag.minimize(Params(precision=0, theta_max=args.theta_max, max_iter=args.fp64_slice))
+        t_sw, n_sw = mag.last_kernel_ms() / 1e3, st["nli"]
+        per_rev, per_sw = t_rev / max(n_rev, 1), t_sw / max(n_sw, 1)
+        est = float(np.sum(np.where(np.arange(len(nli)) == ksw, nli * per_sw, nli * per_rev)))
+        out["plain_fp64_extrapolated"] = {
+            "kernel_s": est, "measured": {"reversible_fields": rev, "reversible_nli": n_rev, "reversible_s": t_rev,
+                                          "switching_field": ksw, "switching_slice_nli": n_sw,
+                                          "switching_slice_s": t_sw},
+            "how": "extrapolated, not measured: sum over the multigrid form's field steps of its NCG iterations x "
+                   "the plain FP64 form's measured seconds per iteration (reversible steps; the switching step "
+                   "from its measured slice)",
+            "speedup_of_precision_multigrid": est / ref["kernel_s"]}
+    if "precision_learned" in forms:
+        t0 = time.perf_counter()
+        net = MLP(device=local_rank, seed=11)
+        Xs, Ts = [], []
+        prm_t = Params(precision=1, amg=1, inner_tol=1e-3)
+        trained_on = []
+        for twl in (synth.hard_cube(n_mag=24, seed=12), synth.polycrystal_cube(n_mag=38, seed=13)):
+            tm = Magnet(device=local_rank)
+            tm.upload_workload(twl)
+            X, T, _ = warmstart.collect(tm, net, twl.m0, twl.fields, tm.sizes()["n_mag"], prm_t)
+            tm.close()
+            Xs.append(X)
+            Ts.append(T)
+            trained_on.append(f"{twl.name} ({len(twl.fields)} fields, {X.shape[0]} node samples)")
+        X, T = torch.cat(Xs), torch.cat(Ts)
+        s_m, s_p, losses = warmstart.train(net, X, T, steps=1500, batch=16384, lr=2e-3, log_every=500)
+        train_s = time.perf_counter() - t0
+        run("precision_learned", mg, net=net, scales=(s_m, s_p))
+        out["precision_learned"]["training"] = {"samples": int(X.shape[0]), "steps": 1500, "seconds": train_s,
+                                                "losses": losses, "trained_on": trained_on,
+                                                "max_change": args.max_change}
+    ref = out.get("plain_fp64") or out.get("precision_multigrid") or out.get("precision")
     for k in ("precision", "precision_multigrid", "precision_learned"):
         if k not in out or out[k] is ref:
             continue
         o = out[k]
-        o["speedup_vs_plain_fp64"] = ref["wall_s"] / o["wall_s"]
+        o["speedup_vs_reference_form"] = ref["wall_s"] / o["wall_s"]
         if o["Hc_T"] is not None and ref["Hc_T"] is not None:
             o["Hc_rel_diff"] = abs(o["Hc_T"] - ref["Hc_T"]) / ref["Hc_T"]
         o["max_abs_dMz"] = float(np.max(np.abs(np.array(o["Mz"]) - np.array(ref["Mz"]))))
-    out["precision_learned"]["training"] = {"samples": int(X.shape[0]), "steps": 1500, "seconds": train_s,
-                                            "losses": losses, "trained_on": coarse.name,
-                                            "max_change": args.max_change}
     if rank == 0:
         print(json.dumps({"mode": "curve", "workload": wl.name, "sizes": sz, "n_fields": len(fields),
-                          "forms": out}))
+                          "reference_form": [k for k in out if out[k] is ref], "forms": out}))
     mag.close()
     return 0
 

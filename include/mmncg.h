@@ -418,6 +418,17 @@ int mm_warmstart_features(mm_ctx* ctx, const double mu0h_next[3], float* X_dev);
 int mm_warmstart_apply(mm_ctx* ctx, mm_mlp* mlp, const double mu0h_next[3],
                        double scale_m, double scale_phi, double max_change);
 
+/* j_max autotuning (Tables 1, 3 and 4 of the paper choose j_max per problem
+ * class by the time to solution): from the current state, minimise the
+ * n_fields applied fields mu0*H (tesla, [n_fields][3]) in turn with p's
+ * parameters and each candidate j_max (candidates [n_candidates], >= 0),
+ * timing the solver launches with CUDA events, and restore the state (m,
+ * potential, applied field) after each trial.  *best_jmax = the fastest
+ * candidate; ms_out [n_candidates] (may be NULL) = each candidate's device
+ * time.  The state is left as it was on entry.  Synchronises. */
+int mm_autotune_jmax(mm_ctx* ctx, const mm_params* p, int64_t n_fields, const double* fields,
+                     const int32_t* candidates, int32_t n_candidates, int32_t* best_jmax, double* ms_out);
+
 /* Device time (ms) of the last persistent-kernel launch, from CUDA events
  * on the context's stream; synchronises. */
 int mm_last_kernel_ms(mm_ctx* ctx, double* ms);

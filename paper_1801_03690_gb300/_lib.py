@@ -84,6 +84,8 @@ EXPORTS = {
     "mm_potential_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mm_demag_curve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(mm_params),
                                  C.POINTER(mm_stats)]),
+    "mm_autotune_jmax": (C.c_int, [C.c_void_p, C.POINTER(mm_params), C.c_int64, C.c_void_p, C.c_void_p,
+                                   C.c_int32, C.POINTER(C.c_int32), C.c_void_p]),
     "mm_last_kernel_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mm_batch_plan": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_double,
                                 C.POINTER(C.c_int32)]),

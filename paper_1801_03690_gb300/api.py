@@ -251,6 +251,18 @@ class Magnet:
         self._check(rc, soft_ok=True)
         return [_stats_dict(s) for s in st]
 
+    def autotune_jmax(self, fields, candidates=(0, 2, 4, 6, 8, 10, 12), params=None):
+        """(best j_max, {j_max: device ms}) over the given field steps from the
+        current state (mm_autotune_jmax); the state is restored."""
+        f = _f64(fields).reshape(-1, 3)
+        c = np.ascontiguousarray(candidates, dtype=np.int32)
+        ms = np.zeros(len(c))
+        best = C.c_int32()
+        p = (params or Params()).to_c()
+        self._check(self._lib.mm_autotune_jmax(self._h, C.byref(p), len(f), _ptr(f), _ptr(c), len(c),
+                                               C.byref(best), _ptr(ms)))
+        return best.value, {int(j): float(t) for j, t in zip(c, ms)}
+
     def last_kernel_ms(self):
         ms = C.c_double()
         self._check(self._lib.mm_last_kernel_ms(self._h, C.byref(ms)))

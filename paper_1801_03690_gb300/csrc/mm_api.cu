@@ -1655,6 +1655,72 @@ int mm_demag_curve(mm_ctx* ctx, int64_t n_fields, const double* fields, const mm
     return first;
 }
 
+int mm_autotune_jmax(mm_ctx* ctx, const mm_params* p, int64_t n_fields, const double* fields,
+                     const int32_t* candidates, int32_t n_candidates, int32_t* best_jmax, double* ms_out) {
+    int rc = need_mesh(ctx);
+    if (rc) return rc;
+    if (n_fields < 1 || !fields || !candidates || n_candidates < 1 || !best_jmax)
+        return fail(ctx, MM_ERR_ARG, "bad autotune arguments");
+    for (int32_t c = 0; c < n_candidates; ++c)
+        if (candidates[c] < 0) return fail(ctx, MM_ERR_ARG, "candidate j_max must be >= 0");
+    if ((rc = check_params(ctx, p))) return rc;
+    mm_params q;
+    if (p) q = *p;
+    else mm_default_params(&q);
+    // the state every trial starts from: m and potential of the current
+    // slot, the applied field
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int cur = ctx->h_state->cur;
+    const size_t v3 = 3 * (size_t)ctx->nm, np = (size_t)ctx->nphi;
+    double* save = nullptr;
+    CK_CUDA(cudaMalloc(&save, (v3 + 2 * np) * sizeof(double)));
+    auto restore = [&]() -> int {
+        CK_CUDA(cudaMemcpyAsync(ctx->P.X[cur], save, v3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK_CUDA(cudaMemcpyAsync(ctx->P.PHI[cur], save + v3, np * sizeof(double), cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+        CK_CUDA(cudaMemcpyAsync(ctx->P.phi, save + v3 + np, np * sizeof(double), cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+        k_set_cur<<<1, 1, 0, ctx->stream>>>(ctx->d_state, cur);
+        CK_CUDA(cudaGetLastError());
+        ctx->has_eval = false;
+        return MM_OK;
+    };
+    CK_CUDA(cudaMemcpyAsync(save, ctx->P.X[cur], v3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK_CUDA(cudaMemcpyAsync(save + v3, ctx->P.PHI[cur], np * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK_CUDA(cudaMemcpyAsync(save + v3 + np, ctx->P.phi, np * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    const double f0[3] = {ctx->field_T[0], ctx->field_T[1], ctx->field_T[2]};
+    double best = -1.0;
+    int first_err = MM_OK;
+    for (int32_t c = 0; c < n_candidates && first_err == MM_OK; ++c) {
+        q.jmax = candidates[c];
+        double tot = 0.0;
+        for (int64_t k = 0; k < n_fields; ++k) {
+            if ((rc = mm_set_field(ctx, fields + 3 * k))) break;
+            if ((rc = mm_minimize_async(ctx, &q))) break;
+            mm_stats st;
+            rc = mm_get_stats(ctx, &st);
+            if (rc < 0) break;
+            double ms = 0.0;
+            if ((rc = mm_last_kernel_ms(ctx, &ms))) break;
+            tot += ms;
+            rc = MM_OK;
+        }
+        if (rc < 0) first_err = rc;
+        if (rc >= 0 && (best < 0.0 || tot < best)) {
+            best = tot;
+            *best_jmax = candidates[c];
+        }
+        if (ms_out) ms_out[c] = tot;
+        const int rr = restore();
+        if (rr && first_err == MM_OK) first_err = rr;
+    }
+    if (first_err == MM_OK) first_err = mm_set_field(ctx, f0);
+    CK_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->h_state->cur = cur;              // the host mirror of the restored slot
+    cudaFree(save);
+    return first_err;
+}
+
 int mm_last_kernel_ms(mm_ctx* ctx, double* ms) {
     if (!ctx || !ms) return MM_ERR_ARG;
     if (!ctx->timed) return fail(ctx, MM_ERR_STATE, "no kernel launched yet");

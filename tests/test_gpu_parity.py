@@ -372,3 +372,33 @@ def test_poisson_schedule_keeps_the_minimum(lib, prec, amg):
         for k in ("nli", "evals", "li", "ls_extra"):
             assert s1[k] == r.stats[k], (k, s1[k], r.stats[k])
     mag.close()
+
+
+def test_jmax_autotune_restores_the_state(lib):
+    """mm_autotune_jmax times the candidates on the given field steps from
+    the current state and leaves that state unchanged; the minimisation
+    afterwards is the same as without the autotuning."""
+    Magnet, Params = lib
+    wl = synth.hard_cube(n_mag=10)
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    mag.set_magnetization(wl.m0)
+    mag.set_field(wl.fields[2])
+    mag.minimize(Params())
+    m_before = mag.get_magnetization()
+    best, ms = mag.autotune_jmax(wl.fields[3:6], candidates=(0, 2, 4, 8))
+    assert best in (0, 2, 4, 8) and all(t > 0 for t in ms.values())
+    assert ms[best] == min(ms.values())
+    np.testing.assert_array_equal(mag.get_magnetization(), m_before)
+    mag.set_field(wl.fields[3])
+    st_a = mag.minimize(Params())
+    m_a = mag.get_magnetization()
+    mag2 = Magnet(device=0)
+    mag2.upload_workload(wl)
+    mag2.set_magnetization(m_before)
+    mag2.set_field(wl.fields[3])
+    st_b = mag2.minimize(Params())
+    assert st_a["F"] == pytest.approx(st_b["F"], rel=1e-9)          # (different potential warm starts)
+    assert np.abs(m_a - mag2.get_magnetization()).max() < 1e-6
+    mag.close()
+    mag2.close()
