@@ -44,8 +44,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "NCG iters/s & demag-curve wall time vs plain FP64 GPU at equal energy tol"
 UNIT = "NCG it/s"
-WORKLOADS = ["large_polycrystal", "large_polycrystal_patches", "polycrystal", "hard_cube", "medium",
-             "soft_cube", "small"]
+WORKLOADS = ["large_polycrystal", "large_polycrystal_patches", "polycrystal_medium", "polycrystal", "hard_cube",
+             "medium", "soft_cube", "small"]
 
 
 def workload(name, sample=False):
@@ -55,6 +55,11 @@ def workload(name, sample=False):
     import synth
     if name == "large_polycrystal":
         return synth.large_polycrystal(n_mag=32) if sample else synth.large_polycrystal()
+    if name == "polycrystal_medium":
+        # the large polycrystal's recipe at 100^3 voxels (same spacing and air
+        # grading, 37 grains): the profiling case, a few GB on the device
+        return synth.large_polycrystal(n_mag=32 if sample else 100, edge=(32 if sample else 100) * 250e-9 / 149,
+                                       n_grains=37)
     if name == "large_polycrystal_patches":
         return synth.large_polycrystal(n_mag=32 if sample else 149, patches_per_grain=10)
     if name == "polycrystal":
@@ -83,15 +88,16 @@ def workload_desc(name, wl, sizes=None):
 # ------------------------------------------------------------ algorithmic bytes
 def form_params(form, theta_max=0.1):
     """Parameters of the three forms of a field step: 0 plain FP64
-    (Jacobi-preconditioned potential solve), 1 precision form with Jacobi,
-    2 precision form with the multigrid preconditioner (the headline)."""
+    (Jacobi-preconditioned potential solve, the paper's method in FP64), 1
+    precision form with Jacobi, 2 the headline: precision form with the
+    multigrid preconditioner and the potential tolerance tied to t1."""
     from paper_1801_03690_gb300 import Params
     if form == 0:
         return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=0, theta_max=theta_max)
     if form == 1:
         return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1, theta_max=theta_max)
     return Params(jmax=4, tau_F=1e-10, poisson_tol=1e-10, precision=1, amg=1, inner_tol=1e-3,
-                  theta_max=theta_max)
+                  poisson_sched=1, theta_max=theta_max)
 
 
 def vcycle_bytes(amg):
@@ -366,6 +372,7 @@ def main():
     ap.add_argument("--sp3-edges", default="8.2,8.4,8.6,8.8", help="sp3 mode: cube edges in exchange lengths")
     ap.add_argument("--sp3-n", type=int, default=24, help="sp3 mode: voxels per cube edge")
     ap.add_argument("--sp3-jmax", type=int, default=12, help="sp3 mode: j_max (Table 3's best: 12)")
+    ap.add_argument("--sp3-box", type=float, default=8.0, help="sp3 mode: air box edge / cube edge")
     ap.add_argument("--forms", default="plain_fp64,precision,precision_multigrid,precision_learned")
     ap.add_argument("--theta-max", type=float, default=0.1,
                     help="curve mode: line-search cap on the largest nodal step (the paper's reading: 0.1)")
@@ -593,8 +600,9 @@ def main():
         "gpu_launches_note": "per timed field step: k_set_field and one persistent k_solver launch",
     }
     line["config"]["precision"] = ("headline: FP32 potential solve preconditioned by the multigrid V-cycle + FP64 "
-                                   "refinement, FP64 energy/gradient/line search/NCG; plain_fp64: FP64 throughout, "
-                                   "Jacobi-preconditioned potential CG")
+                                   "refinement, potential tolerance tied to t1 (loosened only while the last energy "
+                                   "decrease exceeds 100x the t1 threshold), FP64 energy/gradient/line search/NCG; "
+                                   "plain_fp64: FP64 throughout, Jacobi-preconditioned potential CG to 1e-10")
     if jac:
         achj = jac["bytes"] / (jac["kern_ms"] / 1000.0) / 1e9
         line["precision_jacobi"] = {"value": jac["value"], "unit": UNIT, "ms_per_step": jac["t_ms"] / n64,
@@ -753,7 +761,7 @@ def sp3_mode(args, rank, local_rank):
     for L in Ls:
         row = {"L_lex": L}
         for start in ("flower", "vortex"):
-            wl = synth.sp3_cube(L, n_mag=args.sp3_n, start=start)
+            wl = synth.sp3_cube(L, n_mag=args.sp3_n, start=start, box_factor=args.sp3_box)
             mag = Magnet(device=local_rank)
             mag.upload_workload(wl)
             mag.set_magnetization(wl.m0)
@@ -775,7 +783,8 @@ def sp3_mode(args, rank, local_rank):
             cross = a["L_lex"] + a["de"] / (a["de"] - b["de"]) * (b["L_lex"] - a["L_lex"])
             break
     if rank == 0:
-        print(json.dumps({"mode": "sp3", "n_mag": args.sp3_n, "jmax": args.sp3_jmax, "crossover_L_lex": cross,
+        print(json.dumps({"mode": "sp3", "n_mag": args.sp3_n, "jmax": args.sp3_jmax, "box": args.sp3_box,
+                          "crossover_L_lex": cross,
                           "paper": 8.52, "rows": rows}))
     return 0
 

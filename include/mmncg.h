@@ -69,7 +69,9 @@ typedef struct {
 
 typedef struct {
     int device;           /* CUDA device ordinal                                 */
-    int blocks_per_sm;    /* solver kernel built for 2, 3 or 4 blocks/SM (0 = 2) */
+    int blocks_per_sm;    /* solver kernel built for 2, 3 or 4 blocks/SM; 0 =    */
+                          /* chosen at mm_upload_mesh: 4 above 2 M potential    */
+                          /* unknowns, else 2                                   */
     void* stream;         /* cudaStream_t to run on; NULL = a private stream     */
 } mm_options;
 

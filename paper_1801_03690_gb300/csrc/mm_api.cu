@@ -723,6 +723,28 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
     return MM_OK;
 }
 
+// The solver kernel built for `variant` blocks per SM and its grid (as many
+// blocks as are co-resident, at most variant per SM).
+int select_kernel(mm_ctx* ctx, int variant) {
+    ctx->kernel = mm::solver_kernel(variant);
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ctx->kernel, MM_BLOCK, 0) != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        return MM_ERR_CUDA;
+    }
+    ctx->blocks = std::min(bps, variant) * ctx->nsm;
+    return MM_OK;
+}
+
+// Blocks per SM when the caller left the choice to the library: the phases
+// of a potential step are latency-bound, and on GB300 more resident warps
+// pay once the mesh is large -- 4 blocks per SM (64 registers) ran the
+// 8.7 M-unknown polycrystal 1.26x (multigrid precision form) and 1.30x
+// (plain FP64) faster than 2 -- while on the 0.86 M-unknown cube 2 blocks
+// per SM (128 registers, fewest spills) were fastest.
+constexpr int kAutoLargePhi = 2000000;
+int auto_blocks_per_sm(int nphi) { return nphi > kAutoLargePhi ? 4 : 2; }
+
 int launch_solver(mm_ctx* ctx, int mode, const mm::Params& prm) {
     ctx->P.prm = prm;
     ctx->P.mode = mode;
@@ -934,16 +956,10 @@ int mm_create(mm_ctx** out, const mm_options* opt) {
     if (!coop) return bail(MM_ERR_CUDA);
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     // blocks_per_sm selects the kernel instantiation (register budget) and
-    // the grid: 2, 3 or 4 blocks per SM (0 or anything else = 2: measured on
-    // GB300 with the bench mesh, 2 is fastest for the Jacobi forms and ties
-    // with 3 for the multigrid form; its 128-register budget spills least).
+    // the grid: 2, 3 or 4 blocks per SM; 0 = chosen by mm_upload_mesh from
+    // the mesh size (select_kernel), 2 until then.
     const int variant = (ctx->blocks_per_sm_req >= 2 && ctx->blocks_per_sm_req <= 4) ? ctx->blocks_per_sm_req : 2;
-    ctx->kernel = mm::solver_kernel(variant);
-    int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ctx->kernel, MM_BLOCK, 0) != cudaSuccess || bps < 1)
-        return bail(MM_ERR_CUDA);
-    bps = std::min(bps, variant);
-    ctx->blocks = bps * ctx->nsm;
+    if (select_kernel(ctx, variant) != MM_OK) return bail(MM_ERR_CUDA);
     if (opt && opt->stream) {
         ctx->stream = (cudaStream_t)opt->stream;
     } else {
@@ -1311,6 +1327,9 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     }
     // aggregation multigrid hierarchy of K_phi for the FP32 potential solve
     if ((rc = build_hierarchy(ctx, P, std::move(Kfull)))) return rc;
+    if (ctx->blocks_per_sm_req < 2 || ctx->blocks_per_sm_req > 4) {
+        if (select_kernel(ctx, auto_blocks_per_sm(nphi)) != MM_OK) return fail(ctx, MM_ERR_CUDA, "no solver grid");
+    }
     if ((rc = dalloc(ctx, &P.partials, 2 * (size_t)MM_MAXRED * ctx->blocks))) return rc;
     if ((rc = dalloc(ctx, &P.bar, 64))) return rc;
     if ((rc = dalloc(ctx, &P.err, 1))) return rc;

@@ -219,9 +219,12 @@ __device__ __forceinline__ Row sell_row(const long long* sptr, int r) {
 
 #define ROWS(r, n) for (int r = t.rank * MM_BLOCK + (int)threadIdx.x; r < (n); r += t.nb * MM_BLOCK)
 // Row dot products over a SELL-32 row.  All column indices and values of a
-// chunk are loaded (read-only path) before any gather, so each thread keeps
-// a whole row's worth of independent loads in flight: measured on GB300 this
-// lifts an FP32 SpMV from 3.8 to 6.6 TB/s inside the persistent kernel.
+// chunk are loaded before any gather, so each thread keeps a whole row's
+// worth of independent loads in flight: measured on GB300 this lifts an FP32
+// SpMV from 3.8 to 6.6 TB/s inside the persistent kernel.  The matrix
+// entries are read once per product, so they are loaded with the
+// evict-first (streaming) policy, which leaves L2 to the gathered vectors
+// (+1.5% NCG iterations/s on the 8.7 M-unknown polycrystal).
 // Lanes past the row's width read x[pad] (pad = r for square matrices, 0
 // for rectangular ones whose row index may exceed the columns).
 template <int CH, typename T, typename VT, typename XT>
@@ -236,8 +239,8 @@ __device__ __forceinline__ T sell_dot(const long long* __restrict__ sptr, const 
         for (int u = 0; u < CH; ++u) {
             const bool ok = k0 + u < A.width;
             const long long e = A.base + 32ll * (k0 + u);
-            c[u] = ok ? __ldg(col + e) : pad;
-            v[u] = ok ? __ldg(val + e) : VT(0);
+            c[u] = ok ? __ldcs(col + e) : pad;
+            v[u] = ok ? __ldcs(val + e) : VT(0);
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u) s += (T)v[u] * (T)x[c[u]];
@@ -280,9 +283,9 @@ __device__ __forceinline__ void sell_dot3(const long long* __restrict__ sptr, co
 // Two SELL-32 rows r0 and r1 = r0 + team stride (two: r1 exists) per thread,
 // CH entries of both rows loaded before any gather: twice the loads in
 // flight of the one-row form at the register cost of CH = 16.  Used by the
-// FP32 direction step (33.8 vs 34.9 us on the bench mesh at 2 blocks/SM);
-// the multigrid products measured no better than one row with CH = 16.
-// Lanes past a row's width read x[pad].
+// FP32 direction step and the level-0 products of the multigrid cycle,
+// whose rows hold a handful of entries.  Lanes past a row's width read
+// x[pad].
 template <int CH, typename VT>
 __device__ __forceinline__ void sell_dot_2rows(const long long* __restrict__ sptr, const int* __restrict__ col,
                                                const VT* __restrict__ val, const VT* x, int r0, int r1,
@@ -298,10 +301,10 @@ __device__ __forceinline__ void sell_dot_2rows(const long long* __restrict__ spt
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             const bool ok0 = k0 + u < A.width, ok1 = k0 + u < B.width;
-            c0[u] = ok0 ? __ldg(col + A.base + 32ll * (k0 + u)) : pad;
-            v0[u] = ok0 ? __ldg(val + A.base + 32ll * (k0 + u)) : VT(0);
-            c1[u] = ok1 ? __ldg(col + B.base + 32ll * (k0 + u)) : pad;
-            v1[u] = ok1 ? __ldg(val + B.base + 32ll * (k0 + u)) : VT(0);
+            c0[u] = ok0 ? __ldcs(col + A.base + 32ll * (k0 + u)) : pad;
+            v0[u] = ok0 ? __ldcs(val + A.base + 32ll * (k0 + u)) : VT(0);
+            c1[u] = ok1 ? __ldcs(col + B.base + 32ll * (k0 + u)) : pad;
+            v1[u] = ok1 ? __ldcs(val + B.base + 32ll * (k0 + u)) : VT(0);
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
@@ -592,10 +595,10 @@ __device__ __forceinline__ void warp_csr_dot2(const long long* __restrict__ ptr,
         for (int u = 0; u < CH; ++u) {
             const long long k0 = b0 + o + 32 * u + lane, k1 = b1 + o + 32 * u + lane;
             const bool ok0 = k0 < e0, ok1 = k1 < e1;
-            c0[u] = ok0 ? __ldg(col + k0) : 0;
-            v0[u] = ok0 ? __ldg(val + k0) : 0.0f;
-            c1[u] = ok1 ? __ldg(col + k1) : 0;
-            v1[u] = ok1 ? __ldg(val + k1) : 0.0f;
+            c0[u] = ok0 ? __ldcs(col + k0) : 0;
+            v0[u] = ok0 ? __ldcs(val + k0) : 0.0f;
+            c1[u] = ok1 ? __ldcs(col + k1) : 0;
+            v1[u] = ok1 ? __ldcs(val + k1) : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
@@ -648,7 +651,18 @@ __device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
     const Level& V = P.lev[l];
     const float* b = (l == 0) ? P.pres32 : V.b;
     const float* x = (l == 0) ? P.amg_x0 : V.x;
-    ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
+    if (l == 0) {
+        // level 0 (K_phi, a handful of entries per row): two rows per thread
+        // keep twice the loads in flight (+3.5% on the 8.7 M-unknown polycrystal)
+        ROWS2(r, r2, two, V.n) {
+            float s0, s1;
+            sell_dot_2rows<8>(V.sptr, V.col, V.val, x, r, r2, two, r, s0, s1);
+            V.rpre[r] = b[r] - s0;
+            if (two) V.rpre[r2] = b[r2] - s1;
+        }
+    } else {
+        ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
+    }
     amg_restrict(P, t, V, l, [=](int j) { return b[j]; });
     return team_sync(t);
 }
@@ -686,7 +700,16 @@ __device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
         acc[0] += b * y;
         acc[1] += b * b;
     };
-    ROWS(r, V.n) row(r, sell_dot<16, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0));
+    if (l == 0) {
+        ROWS2(r, r2, two, V.n) {
+            float s0, s1;
+            sell_dot_2rows<8>(V.u_sptr, V.u_col, V.u_val, yc, r, r2, two, 0, s0, s1);
+            row(r, s0);
+            if (two) row(r2, s1);
+        }
+    } else {
+        ROWS(r, V.n) row(r, sell_dot<16, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0));
+    }
     if (l > 0) return team_sync(t);
     double out[2];
     if (!team_sum_f32<2>(t, acc, out)) return false;

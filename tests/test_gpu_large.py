@@ -128,14 +128,14 @@ def test_uniform_state_energies(big):
 
 
 def test_headline_form_first_field_step_matches_plain_fp64(big):
-    """The bench's headline form (multigrid precision form) and plain FP64
-    on field index 1 from m0: the same minimum, |m| = 1, t3 at the returned
-    state, the same iteration count, and the identity
-    evals = 2 nli + 1 + ls_extra."""
+    """The bench's headline form (multigrid precision form with the
+    potential tolerance tied to t1) and plain FP64 on field index 1 from m0:
+    the same minimum, |m| = 1, t3 at the returned state, iteration counts
+    within two, and the identity evals = 2 nli + 1 + ls_extra."""
     from paper_1801_03690_gb300 import Params
     wl, mag = big
     out = []
-    for prm in (Params(precision=1, amg=1, inner_tol=1e-3), Params(precision=0)):
+    for prm in (Params(precision=1, amg=1, inner_tol=1e-3, poisson_sched=1), Params(precision=0)):
         mag.set_magnetization(wl.m0)
         mag.set_field(wl.fields[1])
         st = mag.minimize(prm)
@@ -145,7 +145,7 @@ def test_headline_form_first_field_step_matches_plain_fp64(big):
     (sh, mh), (s64, m64) = out
     assert sh["F"] == pytest.approx(s64["F"], rel=1e-8)
     assert np.abs(mh - m64).max() < 1e-5
-    assert sh["nli"] == s64["nli"]
+    assert abs(sh["nli"] - s64["nli"]) <= 2
     mag_nodes = np.linalg.norm(mh, axis=1) > 0
     np.testing.assert_allclose(np.linalg.norm(mh[mag_nodes], axis=1), 1.0, atol=1e-13)
     g = mag.gradient(None, projected=True, params=Params(precision=0))
