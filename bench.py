@@ -363,7 +363,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-curve", action="store_true", help="skip the full hard-cube curves")
-    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling", "sp3"],
+    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling", "sp3", "mlp"],
                     help="steps: the timed field steps (default line); curve: full demagnetisation "
                          "curves of the plain FP64, precision and precision + learned forms; "
                          "batch: the batched platelet workload; scaling: field steps of the hard "
@@ -373,6 +373,7 @@ def main():
     ap.add_argument("--sp3-n", type=int, default=24, help="sp3 mode: voxels per cube edge")
     ap.add_argument("--sp3-jmax", type=int, default=12, help="sp3 mode: j_max (Table 3's best: 12)")
     ap.add_argument("--sp3-box", type=float, default=8.0, help="sp3 mode: air box edge / cube edge")
+    ap.add_argument("--mlp-rows", type=int, default=3375000, help="mlp mode: rows per forward pass")
     ap.add_argument("--forms", default="plain_fp64,precision,precision_multigrid,precision_learned")
     ap.add_argument("--theta-max", type=float, default=0.1,
                     help="curve mode: line-search cap on the largest nodal step (the paper's reading: 0.1)")
@@ -430,6 +431,8 @@ def main():
         return scaling_mode(args, rank, local_rank)
     if args.mode == "sp3":
         return sp3_mode(args, rank, local_rank)
+    if args.mode == "mlp":
+        return mlp_mode(args, rank, local_rank)
 
     t0 = time.perf_counter()
     wl = workload(args.workload)
@@ -743,6 +746,53 @@ def curve_mode(args, rank, local_rank):
         print(json.dumps({"mode": "curve", "workload": wl.name, "sizes": sz, "n_fields": len(fields),
                           "reference_form": [k for k in out if out[k] is ref], "forms": out}))
     mag.close()
+    return 0
+
+
+def mlp_mode(args, rank, local_rank):
+    """The warm-start network alone: forward passes over --mlp-rows rows
+    (default: the large polycrystal's 3,375,000 magnetic nodes) on the
+    tcgen05 path and on the mma.sync path, and Adam training steps on
+    16,384-row mini-batches; device time from CUDA events on the library's
+    stream (synchronised calls), and the tensor work per pass
+    (2 x 128 x (16 + 128 + 128 + 16) multiply-adds per row, the last layer
+    padded to N = 16 on tcgen05)."""
+    import torch
+    from paper_1801_03690_gb300 import MLP
+    n = args.mlp_rows
+    net = MLP(device=local_rank, seed=1)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    X = torch.randn((n, 16), device="cuda", generator=g)
+    out = {"mode": "mlp", "rows": n}
+    flop_row = 2 * 128 * (16 + 128 + 128 + 16)
+    for path, name in ((0, "tcgen05"), (1, "mma.sync")):
+        net.set_tensor_path(path)
+        for _ in range(3):
+            net.forward(X)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 10
+        for _ in range(reps):
+            Y = net.forward(X)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        out[name] = {"ms_per_forward": dt * 1e3, "rows_per_s": n / dt, "tflops": flop_row * n / dt / 1e12,
+                     "checksum": float(Y.double().abs().sum().item())}
+    net.set_tensor_path(0)
+    T = torch.randn((16384, 4), device="cuda", generator=g)
+    xb = X[:16384].contiguous()
+    for _ in range(3):
+        net.train_step(xb, T, 1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(50):
+        net.train_step(xb, T, 1e-3)
+    torch.cuda.synchronize()
+    out["train_step_ms"] = (time.perf_counter() - t0) / 50 * 1e3
+    if rank == 0:
+        print(json.dumps(out))
+    net.close()
     return 0
 
 

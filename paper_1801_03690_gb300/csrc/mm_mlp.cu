@@ -688,7 +688,7 @@ int ensure(mm_mlp* M, long long n) {
 
 int launch_forward(mm_mlp* M, const float* X, long long n, float* Y, bool train) {
     if (M->path == 0) {
-        const int grid = std::max(1, std::min((int)((n + tc::TM - 1) / tc::TM), M->nsm));
+        const int grid = std::max(1, std::min((int)((n + tc::TM - 1) / tc::TM), 2 * M->nsm));
         tc::k_mlp_forward_tc<<<grid, tc::TM, sizeof(tc::Smem), M->stream>>>(
             n, X, M->wb, M->p, M->norm, Y, train ? M->A1 : nullptr, train ? M->A2 : nullptr,
             train ? M->A3 : nullptr, train ? M->X0 : nullptr, M->d_err);
@@ -792,7 +792,9 @@ int mm_mlp_create(mm_mlp** out, int device, uint64_t seed) {
         cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem()) !=
             cudaSuccess ||
         cudaFuncSetAttribute(tc::k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(tc::Smem)) != cudaSuccess)
+                             (int)sizeof(tc::Smem)) != cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_mlp_forward_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+            cudaSuccess)
         return bail(MM_ERR_CUDA);
     // He-uniform initialisation (host RNG, seeded), zero biases
     std::vector<float> h(NPARAM, 0.0f);

@@ -160,7 +160,9 @@ __device__ __forceinline__ void hidden_epilogue(Smem& s, unsigned tlane, const f
     }
 }
 
-__global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(long long n, const float* __restrict__ X,
+// Two CTAs per SM (2 x 110 KB of shared memory, 2 x 128 TMEM columns): while
+// one waits on its MMAs or runs its epilogue, the other's MMAs run.
+__global__ void __launch_bounds__(TM, 2) k_mlp_forward_tc(long long n, const float* __restrict__ X,
                                                            const __nv_bfloat16* __restrict__ wb,
                                                            const float* __restrict__ p,
                                                            const float* __restrict__ norm, float* __restrict__ Y,
