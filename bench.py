@@ -102,15 +102,15 @@ def form_params(form, theta_max=0.1):
 
 def vcycle_bytes(amg):
     """Bytes of one multigrid V-cycle (levels l < L smoothed, L dense):
-      down_l  8 nnz_A_l + 12 n_l + 8 nnz_U_l + 12 n_{l+1} (4 n_L at the last)
-              (A and U^T val+col; x, b read, rpre written; b, x of l+1 written)
+      down_l  8 nnz_A_l + 12 n_l + 8 nnz_P_l + 12 n_{l+1} (4 n_L at the last)
+              (A and P^T val+col; x, b read, rpre written; b, x of l+1 written)
       dense   4 n_L^2 + 8 n_L
       up_l    8 nnz_U_l + 4 n_{l+1} + 16 n_l (U; y_{l+1}; b, rpre, diag^-1 -> y)"""
     L = len(amg) - 1
     tot = 4 * amg[L]["nnz_a"] + 8 * amg[L]["rows"]
     for l in range(L):
         n, nc = amg[l]["rows"], amg[l + 1]["rows"]
-        tot += 8 * amg[l]["nnz_a"] + 12 * n + 8 * amg[l]["nnz_u"] + (4 if l + 1 == L else 12) * nc
+        tot += 8 * amg[l]["nnz_a"] + 12 * n + 8 * amg[l]["nnz_p"] + (4 if l + 1 == L else 12) * nc
         tot += 8 * amg[l]["nnz_u"] + 4 * nc + 16 * n
     return tot
 

@@ -168,10 +168,13 @@ int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi,
  * l = 0..L, rows[l] the rows of level l (level L is the coarsest, solved
  * with a dense inverse), nnz_a[l] the nonzeros of its operator (level 0:
  * K_phi; level L: rows[L]^2 entries of the dense inverse) and, for l < L,
- * nnz_u[l] the nonzeros of its smoothed prolongation U_l.  Any output may
- * be NULL; at most max_entries entries are written per array. */
+ * nnz_u[l] the nonzeros of U_l (the prolongation with the post-smoothing
+ * step folded in, applied in the up phase) and nnz_p[l] those of the
+ * smoothed prolongation P_l (its transpose restricts the pre-smoothed
+ * residual in the down phase).  Any output may be NULL; at most
+ * max_entries entries are written per array. */
 int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nnz_a,
-                int64_t* nnz_u, int32_t max_entries);
+                int64_t* nnz_u, int64_t* nnz_p, int32_t max_entries);
 
 /* Host only (no GPU, no context): build the multigrid hierarchy that
  * mm_upload_mesh builds for K_phi, for the symmetric positive definite

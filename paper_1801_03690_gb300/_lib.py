@@ -61,7 +61,7 @@ EXPORTS = {
                                  C.c_void_p, C.c_int32, C.POINTER(mm_material)]),
     "mm_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int64)] * 4),
     "mm_amg_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
-                              C.POINTER(C.c_int64), C.c_int32]),
+                              C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
     "mm_amg_host_apply": (C.c_int, [C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64),

@@ -130,13 +130,15 @@ class Magnet:
 
     def amg_info(self):
         """Per level of the multigrid hierarchy: rows, nonzeros of the
-        operator (nnz_a; the coarsest: entries of its dense inverse) and of
-        the smoothed prolongation (nnz_u; None at the coarsest)."""
+        operator (nnz_a; the coarsest: entries of its dense inverse), of U
+        (nnz_u, the up phase's prolongation) and of the smoothed prolongation
+        P (nnz_p, whose transpose restricts); None at the coarsest."""
         n = C.c_int32()
-        rows, na, nu = [(C.c_int64 * 64)() for _ in range(3)]
-        self._check(self._lib.mm_amg_info(self._h, C.byref(n), rows, na, nu, 64))
+        rows, na, nu, npp = [(C.c_int64 * 64)() for _ in range(4)]
+        self._check(self._lib.mm_amg_info(self._h, C.byref(n), rows, na, nu, npp, 64))
         L = n.value
-        return [{"rows": int(rows[l]), "nnz_a": int(na[l]), "nnz_u": int(nu[l]) if l < L else None}
+        return [{"rows": int(rows[l]), "nnz_a": int(na[l]), "nnz_u": int(nu[l]) if l < L else None,
+                 "nnz_p": int(npp[l]) if l < L else None}
                 for l in range(L + 1)] if L > 0 else []
 
     # ----------------------------------------------------------------- state

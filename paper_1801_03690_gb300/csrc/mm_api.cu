@@ -107,7 +107,7 @@ struct mm_ctx {
     int nm = 0, nphi = 0;
     long long nnzm = 0, nnzp = 0;         // padded SELL entries
     long long nnzm_true = 0, nnzp_true = 0;
-    std::vector<long long> amg_nnz_a, amg_nnz_u;   // per multigrid level (host copy)
+    std::vector<long long> amg_nnz_a, amg_nnz_u, amg_nnz_p;   // per multigrid level (host copy)
     double Mref = 0.0;
     double field_T[3] = {0, 0, 0};
     std::vector<void*> allocs;            // device buffers of the mesh
@@ -548,7 +548,7 @@ constexpr double kAmgOmegaRho = 1.95;   // ... 1.95 / rho (rho >= the spectral r
 // 23 with w_p = 4 / (3 rho), omega = 0.8.)
 struct AmgHostLevel {
     double omega;
-    HostCsr A, U, Ut;
+    HostCsr A, U, Pt;                    // Pt: the restriction P^T (CSR)
     std::vector<double> dinv;
 };
 
@@ -597,7 +597,7 @@ bool build_amg_host(HostCsr A, AmgHost& H) {
         AmgHostLevel h;
         h.omega = std::min(kAmgOmega, kAmgOmegaRho / rho);
         h.U = minus_scaled_rows(Pm, h.omega, dinv, AP);
-        h.Ut = transpose(h.U);
+        h.Pt = transpose(Pm);
         h.dinv.swap(dinv);
         h.A = std::move(A);
         H.lev.push_back(std::move(h));
@@ -613,7 +613,7 @@ bool build_amg_host(HostCsr A, AmgHost& H) {
 }
 
 // The V-cycle of the device (struct Level) on the host, FP64:
-// x = omega D^-1 b, rpre = b - A x, y_{l+1} = cycle(U^T b),
+// x = omega D^-1 b, rpre = b - A x, y_{l+1} = cycle(P^T rpre),
 // y = omega D^-1 (b + rpre) + U y_{l+1}; the coarsest level y = A^-1 b.
 void amg_host_vcycle(const AmgHost& H, size_t l, const double* b, double* y) {
     if (l == H.lev.size()) {
@@ -634,9 +634,9 @@ void amg_host_vcycle(const AmgHost& H, size_t l, const double* b, double* y) {
         for (long long e = V.A.ptr[i]; e < V.A.ptr[i + 1]; ++e) s += V.A.val[e] * x[V.A.col[e]];
         rpre[i] = b[i] - s;
     }
-    for (int I = 0; I < nc; ++I) {
+    for (int I = 0; I < nc; ++I) {                      // P^T (b - A x) = U^T b
         double s = 0.0;
-        for (long long e = V.Ut.ptr[I]; e < V.Ut.ptr[I + 1]; ++e) s += V.Ut.val[e] * b[V.Ut.col[e]];
+        for (long long e = V.Pt.ptr[I]; e < V.Pt.ptr[I + 1]; ++e) s += V.Pt.val[e] * rpre[V.Pt.col[e]];
         bc[I] = s;
     }
     amg_host_vcycle(H, l + 1, bc.data(), yc.data());
@@ -650,7 +650,7 @@ void amg_host_vcycle(const AmgHost& H, size_t l, const double* b, double* y) {
 // The hierarchy of K_phi for the FP32 potential solve: built on the host
 // from A, level 0's operator as assembled (before prune_noise; level 0 of
 // the hierarchy is its pruned form, which the device holds as P.Kp32),
-// uploaded in FP32 (operators SELL-32, U^T CSR).  Leaves P.nlev = 0
+// uploaded in FP32 (operators SELL-32, P^T CSR).  Leaves P.nlev = 0
 // (Jacobi only) when there is none.
 int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
     int rc;
@@ -659,6 +659,7 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
     P.amg_omega = (float)kAmgOmega;
     ctx->amg_nnz_a.clear();
     ctx->amg_nnz_u.clear();
+    ctx->amg_nnz_p.clear();
     const int n0 = P.nphi;
     if (n0 <= kCoarseDense) return MM_OK;
     AmgHost H;
@@ -689,12 +690,12 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
         }
         if ((rc = upload_sell(ctx, h.U, &V.u_sptr, &V.u_col, &V.u_val))) return rc;
         {
-            std::vector<float> tv(h.Ut.val.begin(), h.Ut.val.end());
+            std::vector<float> tv(h.Pt.val.begin(), h.Pt.val.end());
             long long* tp;
             int* tc;
             float* tvd;
-            if ((rc = upload(ctx, &tp, h.Ut.ptr.data(), h.Ut.ptr.size()))) return rc;
-            if ((rc = upload(ctx, &tc, h.Ut.col.data(), h.Ut.col.size()))) return rc;
+            if ((rc = upload(ctx, &tp, h.Pt.ptr.data(), h.Pt.ptr.size()))) return rc;
+            if ((rc = upload(ctx, &tc, h.Pt.col.data(), h.Pt.col.size()))) return rc;
             if ((rc = upload(ctx, &tvd, tv.data(), tv.size()))) return rc;
             V.t_ptr = tp;
             V.t_col = tc;
@@ -718,6 +719,7 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
     for (const AmgHostLevel& h : H.lev) {
         ctx->amg_nnz_a.push_back((long long)h.A.col.size());
         ctx->amg_nnz_u.push_back((long long)h.U.col.size());
+        ctx->amg_nnz_p.push_back((long long)h.Pt.col.size());
     }
     ctx->amg_nnz_a.push_back((long long)H.nco * H.nco);        // the dense inverse
     return MM_OK;
@@ -1427,7 +1429,7 @@ int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi, int64_t* nnz_mag
 }
 
 int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nnz_a, int64_t* nnz_u,
-                int32_t max_entries) {
+                int64_t* nnz_p, int32_t max_entries) {
     if (!ctx || !ctx->has_mesh) return MM_ERR_STATE;
     const mm::Problem& P = ctx->P;
     if (n_levels) *n_levels = P.nlev;
@@ -1436,6 +1438,7 @@ int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nn
         if (rows) rows[l] = (l < P.nlev) ? P.lev[l].n : P.nco;
         if (nnz_a) nnz_a[l] = ctx->amg_nnz_a[l];
         if (nnz_u && l < P.nlev) nnz_u[l] = ctx->amg_nnz_u[l];
+        if (nnz_p && l < P.nlev) nnz_p[l] = ctx->amg_nnz_p[l];
     }
     return MM_OK;
 }

@@ -80,11 +80,12 @@ struct DevState {
 // potential solve (level 0: K_phi itself; level l+1: the Galerkin operator
 // P^T A_l P of the smoothed prolongation P of the aggregates of level l).
 // With x = omega D^-1 b (one damped-Jacobi step from zero), the V-cycle is
-//   down: rpre = b - A x,   b_{l+1} = U^T b
+//   down: rpre = b - A x,   b_{l+1} = P^T rpre
 //   up:   y = omega D^-1 (b + rpre) + U y_{l+1}
 // with U = P - omega D^-1 A P, i.e. pre-smoothing, restriction of the
 // residual, coarse correction and post-smoothing with the same damped
-// Jacobi step: a symmetric operator.  Operators are FP32, SELL-32 except U^T.
+// Jacobi step: a symmetric operator (P^T rpre = U^T b).  Operators are
+// FP32, SELL-32 except P^T (CSR).
 struct Level {
     int n;                   // rows of this level
     int nc;                  // rows of the next coarser level
@@ -95,7 +96,7 @@ struct Level {
     const long long* u_sptr; // U (n rows, nc columns)
     const int* u_col;
     const float* u_val;
-    const long long* t_ptr;  // U^T (nc rows, n columns) in CSR: its rows are wide
+    const long long* t_ptr;  // P^T (nc rows, n columns) in CSR: its rows are wide
     const int* t_col;        // (the support of a smoothed aggregate), one warp
     const float* t_val;      // takes one row
     const float* dinv;       // 1 / diag(A_l)

@@ -613,13 +613,13 @@ __device__ __forceinline__ void warp_csr_dot2(const long long* __restrict__ ptr,
 // ---- smoothed-aggregation multigrid V-cycle (the FP32 solve's
 // preconditioner when a hierarchy exists and prm.amg is set); operators as
 // in struct Level.  A down phase computes rpre = b - A x on the rows of its
-// level (one thread per row) and b_{l+1} = U^T b, x_{l+1} = omega D^-1
-// b_{l+1} on the rows of the next level (one warp per row, two rows at a
-// time).  The warps take the coarse rows from the end of the grid, so on
-// the small levels, where the fine rows occupy only the first blocks, both
-// parts run side by side.
+// level (one thread per row), then, after a team barrier, b_{l+1} = P^T rpre
+// and x_{l+1} = omega D^-1 b_{l+1} on the rows of the next level (one warp
+// per row, two rows at a time).  The warps take the coarse rows from the end
+// of the grid, so that on the small levels they are not the blocks that
+// hold the fine rows.
 
-// Restriction rows of a down phase: b_{l+1} = U^T b with b(j) given by bx.
+// Restriction rows of a down phase: b_{l+1} = P^T r with r(j) given by bx.
 template <class XF>
 __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, const Level& V, int l, XF bx) {
     const bool last = (l + 1 == P.nlev);
@@ -644,7 +644,11 @@ __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, co
 }
 
 // Down phase of level l; at level 0, b is the FP32 residual and x = omega
-// D^-1 b has been written with it by the update step.
+// D^-1 b has been written with it by the update step.  The pre-smoothed
+// residual rpre is restricted after a team barrier with P^T, which holds
+// half the entries of U^T (U^T b, the same vector, needs no barrier:
+// measured on the 8.7 M-unknown polycrystal, the U^T restriction took 205
+// of the phase's 323 us).
 __device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
     const Problem& P = *C.P;
     Team& t = C.t;
@@ -663,7 +667,9 @@ __device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
     } else {
         ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
     }
-    amg_restrict(P, t, V, l, [=](int j) { return b[j]; });
+    if (!team_sync(t)) return false;
+    const float* rp = V.rpre;
+    amg_restrict(P, t, V, l, [=](int j) { return rp[j]; });
     return team_sync(t);
 }
 

@@ -17,15 +17,16 @@ def bench():
     return mod
 
 
-LEVELS = [{"rows": 1000, "nnz_a": 15000, "nnz_u": 9000},
-          {"rows": 40, "nnz_a": 1600, "nnz_u": 500},
-          {"rows": 3, "nnz_a": 9, "nnz_u": None}]
+LEVELS = [{"rows": 1000, "nnz_a": 15000, "nnz_u": 9000, "nnz_p": 4000},
+          {"rows": 40, "nnz_a": 1600, "nnz_u": 500, "nnz_p": 300},
+          {"rows": 3, "nnz_a": 9, "nnz_u": None, "nnz_p": None}]
 
 
 def test_vcycle_bytes(bench):
-    # level 0: 8*15000 + 16*9000 + 28*1000 + 16*40; level 1 (last smoothed):
-    # 8*1600 + 16*500 + 28*40 + 8*3; dense coarsest 4*9 + 8*3
-    want = (8 * 15000 + 16 * 9000 + 28 * 1000 + 16 * 40) + (8 * 1600 + 16 * 500 + 28 * 40 + 8 * 3) + (4 * 9 + 8 * 3)
+    # level 0: 8*15000 + 8*4000 (P^T) + 8*9000 (U) + 28*1000 + 16*40; level 1
+    # (last smoothed): 8*1600 + 8*300 + 8*500 + 28*40 + 8*3; dense coarsest 4*9 + 8*3
+    want = ((8 * 15000 + 8 * 4000 + 8 * 9000 + 28 * 1000 + 16 * 40) + (8 * 1600 + 8 * 300 + 8 * 500 + 28 * 40 + 8 * 3)
+            + (4 * 9 + 8 * 3))
     assert bench.vcycle_bytes(LEVELS) == want
 
 
