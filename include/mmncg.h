@@ -364,11 +364,11 @@ int64_t mm_mlp_param_count(void);
 int mm_mlp_create(mm_mlp** mlp, int device, uint64_t seed);
 void mm_mlp_destroy(mm_mlp* mlp);
 int mm_mlp_set_params(mm_mlp* mlp, const float* params, int64_t count);
-/* Tensor-core path of the forward pass: 0 (default) = tcgen05 MMAs with
- * FP32 accumulators in tensor memory (one 128-row tile per MMA), 1 = the
- * warp-level mma.sync path, kept as a measured comparison.  Both round at
- * the same points (BF16 inputs, weights and hidden activations; FP32
- * accumulation).  A tensor-core wait that runs out (2 s) makes the next
+/* Tensor-core path of the forward pass and of the weight gradients: 0
+ * (default) = tcgen05 MMAs with FP32 accumulators in tensor memory (M = 128
+ * per MMA), 1 = the warp-level mma.sync path, kept as a measured
+ * comparison.  Both round at the same points (BF16 inputs, weights and
+ * hidden activations; FP32 accumulation).  A tensor-core wait that runs out (2 s) makes the next
  * synchronising MLP call return MM_ERR_DEVICE_TIMEOUT. */
 int mm_mlp_set_tensor_path(mm_mlp* mlp, int path);
 int mm_mlp_get_params(mm_mlp* mlp, float* params, int64_t count);

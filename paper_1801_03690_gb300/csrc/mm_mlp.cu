@@ -4,11 +4,11 @@
 // of the scalar potential.  Plain NCG then runs to t1-t3 from the corrected
 // state, so the network only changes where the minimiser starts.
 //
-// The forward pass runs on the 5th-generation tensor cores (tcgen05.mma,
-// accumulators in tensor memory: mm_mlp_tc.cuh); the same network on the
-// warp-level mma.sync m16n8k16 path (BF16 operands, FP32 accumulation) is
-// kept as a measured comparison (mm_mlp_set_tensor_path), and the backward
-// kernels use it:
+// The forward pass and the weight gradients run on the 5th-generation
+// tensor cores (tcgen05.mma, accumulators in tensor memory: mm_mlp_tc.cuh);
+// the same network on the warp-level mma.sync m16n8k16 path (BF16 operands,
+// FP32 accumulation) is kept as a measured comparison
+// (mm_mlp_set_tensor_path), and the activation-gradient kernel uses it:
 //   k_mlp_forward   persistent; the weights (BF16, [out][in]) live in shared
 //                   memory; inputs are standardised in FP32 (the network's
 //                   own mean and 1/std) before the BF16 conversion, then each
@@ -721,7 +721,11 @@ int gradient(mm_mlp* M, const float* X, const float* T, long long n) {
                    {NH, NH, OFF_W3, OFF_B3, M->DZ3, M->A2},
                    {NOUT, NH, OFF_W4, OFF_B4, M->DZ4, M->A3}};
     for (auto& l : layers) {
-        k_mlp_wgrad<<<nch, WARPS * 32, wgrad_smem(), M->stream>>>(n, l.nout, l.nin, l.dz, l.a, M->part);
+        if (M->path == 0)
+            tc::k_mlp_wgrad_tc<<<nch, tc::TM, sizeof(tc::WgSmem), M->stream>>>(n, l.nout, l.nin, l.dz, l.a, M->part,
+                                                                              M->d_err);
+        else
+            k_mlp_wgrad<<<nch, WARPS * 32, wgrad_smem(), M->stream>>>(n, l.nout, l.nin, l.dz, l.a, M->part);
         MK(cudaGetLastError());
         const int nw = l.nout * l.nin;
         k_mlp_wreduce<<<(nw + 255) / 256, 256, 0, M->stream>>>(nch, nw, M->part, M->g + l.offw);
@@ -794,7 +798,9 @@ int mm_mlp_create(mm_mlp** out, int device, uint64_t seed) {
         cudaFuncSetAttribute(tc::k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(tc::Smem)) != cudaSuccess ||
         cudaFuncSetAttribute(tc::k_mlp_forward_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_mlp_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(tc::WgSmem)) != cudaSuccess)
         return bail(MM_ERR_CUDA);
     // He-uniform initialisation (host RNG, seeded), zero biases
     std::vector<float> h(NPARAM, 0.0f);

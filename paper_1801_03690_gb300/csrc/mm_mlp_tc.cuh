@@ -1,8 +1,8 @@
-// Forward pass of the warm-start network on the 5th-generation tensor cores
-// (tcgen05): BF16 operands staged in shared memory, FP32 accumulators in
-// tensor memory (TMEM), one 128-row tile per MMA (M = 128, one TMEM lane per
-// row).  Included by mm_mlp.cu (it uses that file's layer sizes and
-// parameter layout).
+// Forward pass and weight gradient of the warm-start network on the
+// 5th-generation tensor cores (tcgen05): BF16 operands staged in shared
+// memory, FP32 accumulators in tensor memory (TMEM), M = 128 per MMA (one
+// TMEM lane per row).  Included by mm_mlp.cu (it uses that file's layer
+// sizes and parameter layout).
 //
 // Per tile of 128 rows (4 warps, thread t owns row t of the tile):
 //   x   = bf16((X - mean) / std)                  -> shared memory
@@ -285,6 +285,97 @@ __global__ void __launch_bounds__(TM, 2) k_mlp_forward_tc(long long n, const flo
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
         wait_phase(&s.bar, parity);       // the phase that did not complete: let it finish (bounded)
+    }
+    before_sync();
+    __syncthreads();
+    after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TCOLS) : "memory");
+}
+
+// ---- weight gradient on tcgen05.  Chunk c of KW = 128 rows gives the
+// partial dW = dZ^T A_prev over its rows as one MMA product of M = 128
+// (outputs; zero rows beyond nout), N = nin padded to 16, K = 128 (rows):
+// both operands are staged transposed (dZ^T: (out, row), A_prev^T: (in,
+// row)) into the K-major core-matrix layout, 8 MMAs of K = 16 accumulate in
+// TMEM, and the epilogue writes partial[c][o][i] (o < nout, i < nin) for the
+// fixed-order reduction over chunks that follows.
+constexpr int KW = 128;
+
+struct __align__(128) WgSmem {
+    __nv_bfloat16 a[TM * KW];
+    __nv_bfloat16 b[TM * KW];
+    unsigned long long bar;
+    unsigned tmem;
+};
+
+__global__ void __launch_bounds__(TM, 2) k_mlp_wgrad_tc(long long n, int nout, int nin,
+                                                         const __nv_bfloat16* __restrict__ DZ,
+                                                         const __nv_bfloat16* __restrict__ A,
+                                                         float* __restrict__ partial, int* err) {
+    extern __shared__ __align__(1024) unsigned char tc_wsmem[];
+    WgSmem& s = *reinterpret_cast<WgSmem*>(tc_wsmem);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int np = (nin + 15) / 16 * 16;
+    const long long r = (long long)blockIdx.x * KW + tid;     // this thread's row of the chunk
+    unsigned char* ab = reinterpret_cast<unsigned char*>(s.a);
+    unsigned char* bb = reinterpret_cast<unsigned char*>(s.b);
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int o = 0; o < TM; ++o)
+        *reinterpret_cast<__nv_bfloat16*>(ab + core_off(o, tid, KW)) =
+            (r < n && o < nout) ? DZ[r * nout + o] : zero;
+    for (int i = 0; i < np; ++i)
+        *reinterpret_cast<__nv_bfloat16*>(bb + core_off(i, tid, KW)) = (r < n && i < nin) ? A[r * nin + i] : zero;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    before_sync();
+    __syncthreads();
+    after_sync();
+    const unsigned tbase = s.tmem;
+    const unsigned tlane = tbase + ((unsigned)(warp * 32) << 16);
+    constexpr unsigned long long KSTEP = 256 >> 4;
+    if (tid == 0) {
+        const unsigned long long da = sdesc(s.a, KW), db = sdesc(s.b, KW);
+        const unsigned id = idesc_bf16(TM, np);
+#pragma unroll
+        for (int k = 0; k < KW / 16; ++k) mma(tbase, da + k * KSTEP, db + k * KSTEP, id, k > 0);
+        commit(&s.bar);
+    }
+    const bool ok = __syncthreads_and(wait_phase(&s.bar, 0u)) != 0;
+    after_sync();
+    if (ok) {
+        float* out = partial + (size_t)blockIdx.x * nout * nin;
+        const int o = tid;                                     // TMEM lane = output row
+        if (np == 16) {
+            float v[16];
+            tmem_ld16(tlane, v);
+            if (o < nout)
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (i < nin) out[o * nin + i] = v[i];
+        } else {
+#pragma unroll 1
+            for (int j = 0; j < np / 32; ++j) {
+                float v[32];
+                tmem_ld32(tlane + 32 * j, v);
+                if (o < nout)
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (32 * j + i < nin) out[o * nin + 32 * j + i] = v[i];
+            }
+        }
+    } else {
+        if (tid == 0) atomicExch(err, 1);
+        wait_phase(&s.bar, 0u);
     }
     before_sync();
     __syncthreads();

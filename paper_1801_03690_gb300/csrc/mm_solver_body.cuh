@@ -566,79 +566,69 @@ __device__ __forceinline__ void dot2_merge(Dot2& d, float p, float s) {
     d.s = __fadd_rn(d.s, __fadd_rn(s, q));
 }
 
-__device__ __forceinline__ float dot2_warp(Dot2 d) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float p = __shfl_xor_sync(0xffffffffu, d.p, o);
-        const float s = __shfl_xor_sync(0xffffffffu, d.s, o);
-        dot2_merge(d, p, s);
-    }
-    return d.p + d.s;
-}
-
-// One warp's dot products of two CSR rows r0, r1 (r1 < 0: none) with x,
-// compensated.  Each lane loads CH entries of both rows (predicated, all
-// issued before any gather) per pass, so a warp keeps two rows' worth of
-// loads in flight.
-template <int CH, class XF>
-__device__ __forceinline__ void warp_csr_dot2(const long long* __restrict__ ptr, const int* __restrict__ col,
-                                              const float* __restrict__ val, XF x, int r0, int r1, int lane,
-                                              float& out0, float& out1) {
-    const long long b0 = ptr[r0], e0 = ptr[r0 + 1];
-    const long long b1 = r1 >= 0 ? ptr[r1] : 0, e1 = r1 >= 0 ? ptr[r1 + 1] : 0;
-    Dot2 s0 = {0.0f, 0.0f}, s1 = {0.0f, 0.0f};
-    const long long span = (e0 - b0 > e1 - b1) ? e0 - b0 : e1 - b1;
-    for (long long o = 0; o < span; o += 32 * CH) {
-        int c0[CH], c1[CH];
-        float v0[CH], v1[CH];
+// The dot product of CSR row `row` (< 0: an empty row) with x, computed by a
+// group of G consecutive lanes (G divides 32): lane gl of the group takes
+// entries gl, gl + G, ..., CH per pass with all of a pass's loads issued
+// before any gather, accumulates them compensated, and the group combines
+// its lanes with a G-lane xor reduction (every lane of the warp takes part).
+#ifndef MM_RESTRICT_G
+#define MM_RESTRICT_G 8
+#endif
+template <int G, int CH, class XF>
+__device__ __forceinline__ float group_csr_dot2(const long long* __restrict__ ptr, const int* __restrict__ col,
+                                                const float* __restrict__ val, XF x, int row, int gl) {
+    const long long b = row >= 0 ? ptr[row] : 0, e = row >= 0 ? ptr[row + 1] : 0;
+    Dot2 s = {0.0f, 0.0f};
+    for (long long o = b + gl; o < e; o += (long long)G * CH) {
+        int c[CH];
+        float v[CH];
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
-            const long long k0 = b0 + o + 32 * u + lane, k1 = b1 + o + 32 * u + lane;
-            const bool ok0 = k0 < e0, ok1 = k1 < e1;
-            c0[u] = ok0 ? __ldcs(col + k0) : 0;
-            v0[u] = ok0 ? __ldcs(val + k0) : 0.0f;
-            c1[u] = ok1 ? __ldcs(col + k1) : 0;
-            v1[u] = ok1 ? __ldcs(val + k1) : 0.0f;
+            const long long k = o + (long long)G * u;
+            const bool ok = k < e;
+            c[u] = ok ? __ldcs(col + k) : 0;
+            v[u] = ok ? __ldcs(val + k) : 0.0f;
         }
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            dot2_add(s0, v0[u], x(c0[u]));
-            dot2_add(s1, v1[u], x(c1[u]));
-        }
+        for (int u = 0; u < CH; ++u) dot2_add(s, v[u], x(c[u]));
     }
-    out0 = dot2_warp(s0);
-    out1 = dot2_warp(s1);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const float p = __shfl_xor_sync(0xffffffffu, s.p, off);
+        const float q = __shfl_xor_sync(0xffffffffu, s.s, off);
+        dot2_merge(s, p, q);
+    }
+    return s.p + s.s;
 }
 
 // ---- smoothed-aggregation multigrid V-cycle (the FP32 solve's
 // preconditioner when a hierarchy exists and prm.amg is set); operators as
 // in struct Level.  A down phase computes rpre = b - A x on the rows of its
 // level (one thread per row), then, after a team barrier, b_{l+1} = P^T rpre
-// and x_{l+1} = omega D^-1 b_{l+1} on the rows of the next level (one warp
-// per row, two rows at a time).  The warps take the coarse rows from the end
-// of the grid, so that on the small levels they are not the blocks that
-// hold the fine rows.
+// and x_{l+1} = omega D^-1 b_{l+1} on the rows of the next level (a group of
+// lanes per row).
 
-// Restriction rows of a down phase: b_{l+1} = P^T r with r(j) given by bx.
+// Restriction rows of a down phase: b_{l+1} = P^T r with r(j) given by bx,
+// x_{l+1} = omega D^-1 b_{l+1}.  A group of MM_RESTRICT_G lanes per coarse
+// row, so a warp works on 32 / G rows at once: the rows of P^T hold tens of
+// entries (2.9 per fine row on the lattice meshes), and a whole warp per
+// row spent its time in the 5-level shuffle reduction.
 template <class XF>
 __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, const Level& V, int l, XF bx) {
+    constexpr int G = MM_RESTRICT_G, RPW = 32 / G;
     const bool last = (l + 1 == P.nlev);
     float* bn = last ? P.bco : P.lev[l + 1].b;
     float* xn = last ? nullptr : P.lev[l + 1].x;
     const float* dn = last ? nullptr : P.lev[l + 1].dinv;
     const float on = last ? 0.0f : P.lev[l + 1].omega;
     const int lane = threadIdx.x & 31, wpb = MM_BLOCK / 32, nw = t.nb * wpb;
-    const int w = nw - 1 - (t.rank * wpb + (int)(threadIdx.x >> 5));
-    for (int I = w; I < V.nc; I += 2 * nw) {
-        const int J = (I + nw < V.nc) ? I + nw : -1;
-        float s0, s1;
-        warp_csr_dot2<8>(V.t_ptr, V.t_col, V.t_val, bx, I, J, lane, s0, s1);
-        if (lane == 0) {
-            bn[I] = s0;
-            if (!last) xn[I] = on * dn[I] * s0;
-        } else if (lane == 1 && J >= 0) {
-            bn[J] = s1;
-            if (!last) xn[J] = on * dn[J] * s1;
+    const int gw = t.rank * wpb + (int)(threadIdx.x >> 5), grp = lane / G, gl = lane % G;
+    for (int I0 = gw * RPW; I0 < V.nc; I0 += nw * RPW) {
+        const int I = I0 + grp;
+        const float s = group_csr_dot2<G, 12>(V.t_ptr, V.t_col, V.t_val, bx, I < V.nc ? I : -1, gl);
+        if (gl == 0 && I < V.nc) {
+            bn[I] = s;
+            if (!last) xn[I] = on * dn[I] * s;
         }
     }
 }

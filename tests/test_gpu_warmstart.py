@@ -195,3 +195,31 @@ def test_tcgen05_forward_matches_reference_and_mma_sync(n):
     print(f"tcgen05 vs mma.sync, n={n}: max {mx:.2e} median {med:.2e} q90 {q90:.2e}")
     assert mx <= 1e-2 and med <= 1e-5
     assert np.isfinite(Y_tc).all()
+
+
+@pytest.mark.parametrize("n", [517, 4096])
+def test_tcgen05_weight_gradient_matches_mma_sync_and_reference(n):
+    """The weight gradients on tcgen05 (one M = 128, K = 128-row MMA product
+    per chunk of rows, default) against the mma.sync path on the same
+    activations (the same FP32 sums of BF16 products) and against the
+    oracle's network gradients."""
+    import torch
+    from paper_1801_03690_gb300 import MLP
+    net = MLP(seed=6)
+    p = net.get_params()
+    rng = np.random.default_rng(8)
+    X = torch.tensor(rng.normal(size=(n, 16)).astype(np.float32), device="cuda")
+    T = torch.tensor(rng.normal(size=(n, 4)).astype(np.float32), device="cuda")
+    g_tc, loss_tc = net.gradient(X, T)
+    net.set_tensor_path(1)
+    g_ms, loss_ms = net.gradient(X, T)
+    net.set_tensor_path(0)
+    assert loss_tc == loss_ms
+    scale = np.abs(g_ms).max()
+    err = np.abs(g_tc - g_ms).max() / scale
+    print(f"tcgen05 vs mma.sync weight gradients, n={n}: max deviation {err:.2e} of the largest")
+    assert err <= 1e-5
+    lr, gr = omlp.loss_and_grads(_params_list(p), X.cpu().numpy().astype(np.float64),
+                                 T.cpu().numpy().astype(np.float64), round_bf16=True)
+    for (gw, gb), (rw, rb) in zip(_params_list(g_tc), gr):
+        np.testing.assert_allclose(gw, rw, rtol=0, atol=3e-2 * np.abs(rw).max())
