@@ -679,7 +679,7 @@ def curve_mode(args, rank, local_rank):
 
     run("plain_fp64", Params(precision=0, theta_max=args.theta_max))
     run("precision", Params(precision=1, theta_max=args.theta_max))
-    mg = Params(precision=1, amg=1, inner_tol=1e-3, theta_max=args.theta_max)
+    mg = form_params(2, theta_max=args.theta_max)       # the headline form (schedule included)
     run("precision_multigrid", mg, keep_states="plain_fp64_extrapolated" in forms)
     if "plain_fp64_extrapolated" in forms and "precision_multigrid" in out:
         ref = out["precision_multigrid"]
@@ -716,7 +716,7 @@ def curve_mode(args, rank, local_rank):
         t0 = time.perf_counter()
         net = MLP(device=local_rank, seed=11)
         Xs, Ts = [], []
-        prm_t = Params(precision=1, amg=1, inner_tol=1e-3)
+        prm_t = form_params(2)
         trained_on = []
         for twl in (synth.hard_cube(n_mag=24, seed=12), synth.polycrystal_cube(n_mag=38, seed=13)):
             tm = Magnet(device=local_rank)
