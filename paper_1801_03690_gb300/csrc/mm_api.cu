@@ -671,6 +671,7 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
         V.n = h.U.n;
         V.nc = h.U.m;
         V.omega = (float)h.omega;
+        V.wide = (h.Pt.n > 0 && (double)h.Pt.col.size() / h.Pt.n > 160.0) ? 1 : 0;
         if (l == 0) {
             V.sptr = P.p_sptr;
             V.col = P.p_col;

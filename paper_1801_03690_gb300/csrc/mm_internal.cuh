@@ -90,6 +90,7 @@ struct Level {
     int n;                   // rows of this level
     int nc;                  // rows of the next coarser level
     float omega;             // Jacobi damping of this level's smoother
+    int wide;                // 1: P^T rows average over 160 entries (a warp per row)
     const long long* sptr;   // A_l (level 0: the FP32 copy of K_phi)
     const int* col;
     const float* val;

@@ -609,13 +609,13 @@ __device__ __forceinline__ float group_csr_dot2(const long long* __restrict__ pt
 // lanes per row).
 
 // Restriction rows of a down phase: b_{l+1} = P^T r with r(j) given by bx,
-// x_{l+1} = omega D^-1 b_{l+1}.  A group of MM_RESTRICT_G lanes per coarse
-// row, so a warp works on 32 / G rows at once: the rows of P^T hold tens of
-// entries (2.9 per fine row on the lattice meshes), and a whole warp per
-// row spent its time in the 5-level shuffle reduction.
-template <class XF>
-__device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, const Level& V, int l, XF bx) {
-    constexpr int G = MM_RESTRICT_G, RPW = 32 / G;
+// x_{l+1} = omega D^-1 b_{l+1}.  A group of G lanes per coarse row, so a
+// warp works on 32 / G rows at once: at the fine end the rows of P^T hold
+// tens of entries (2.9 per fine row on the lattice meshes), and a whole warp
+// per row spent its time in the 5-level shuffle reduction.
+template <int G, class XF>
+__device__ __forceinline__ void amg_restrict_g(const Problem& P, const Team& t, const Level& V, int l, XF bx) {
+    constexpr int RPW = 32 / G;
     const bool last = (l + 1 == P.nlev);
     float* bn = last ? P.bco : P.lev[l + 1].b;
     float* xn = last ? nullptr : P.lev[l + 1].x;
@@ -631,6 +631,17 @@ __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, co
             if (!last) xn[I] = on * dn[I] * s;
         }
     }
+}
+
+// Levels with few, long restriction rows (the coarse end of the hierarchy:
+// hundreds of entries per row, a few hundred rows) take a whole warp per
+// row, the others a group of MM_RESTRICT_G lanes (measured on the 8.7 M-
+// unknown polycrystal: 8 lanes 190 us, 4 lanes 211, 16 lanes 225 for the
+// level-0 down phase).
+template <class XF>
+__device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, const Level& V, int l, XF bx) {
+    if (V.wide) amg_restrict_g<32>(P, t, V, l, bx);
+    else amg_restrict_g<MM_RESTRICT_G>(P, t, V, l, bx);
 }
 
 // Down phase of level l; at level 0, b is the FP32 residual and x = omega
