@@ -170,8 +170,10 @@ def test_tcgen05_forward_matches_reference_and_mma_sync(n):
     hidden activations); they differ in FP32 (GPU) vs FP64 (oracle)
     accumulation order, which moves an output by ~1e-6 of the largest and,
     where a hidden activation lies within that of a BF16 rounding boundary,
-    flips it by one BF16 unit (2^-8 relative): the median deviation must be
-    at rounding level and the largest within a few BF16 units."""
+    flips it by one BF16 unit (2^-8 relative) -- measured: median 5e-9 and
+    largest 9e-4 of the largest output over 20,000 rows; the bound on the
+    largest is 2e-3.  The two GPU paths accumulate the same products in the
+    same order (measured bitwise equal)."""
     import torch
     from paper_1801_03690_gb300 import MLP
     net = MLP(seed=4)
@@ -190,10 +192,10 @@ def test_tcgen05_forward_matches_reference_and_mma_sync(n):
     for name, Y in (("tcgen05", Y_tc), ("mma.sync", Y_ms)):
         mx, med, q90 = _deviation_stats(Y, Yr)
         print(f"{name} vs oracle, n={n}: max {mx:.2e} median {med:.2e} q90 {q90:.2e} (of the largest output)")
-        assert mx <= 1e-2 and med <= 1e-5, (name, mx, med)
+        assert mx <= 2e-3 and med <= 1e-5, (name, mx, med)        # measured: max 9e-4, median 5e-9
     mx, med, q90 = _deviation_stats(Y_tc, Y_ms)
     print(f"tcgen05 vs mma.sync, n={n}: max {mx:.2e} median {med:.2e} q90 {q90:.2e}")
-    assert mx <= 1e-2 and med <= 1e-5
+    assert mx <= 1e-6                                             # measured: bitwise equal
     assert np.isfinite(Y_tc).all()
 
 
