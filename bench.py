@@ -753,8 +753,9 @@ def mlp_mode(args, rank, local_rank):
     """The warm-start network alone: forward passes over --mlp-rows rows
     (default: the large polycrystal's 3,375,000 magnetic nodes) on the
     tcgen05 path and on the mma.sync path, and Adam training steps on
-    16,384-row mini-batches; device time from CUDA events on the library's
-    stream (synchronised calls), and the tensor work per pass
+    16,384-row mini-batches; host wall time over repeated calls bracketed by
+    device synchronisations (the calls synchronise the library's stream
+    themselves), and the tensor work per pass
     (2 x 128 x (16 + 128 + 128 + 16) multiply-adds per row, the last layer
     padded to N = 16 on tcgen05)."""
     import torch
@@ -887,7 +888,8 @@ def scaling_mode(args, rank, local_rank):
 def batch_mode(args, rank, local_rank):
     """The batched sensor workload: n permalloy platelets of 5k-80k magnetic
     nodes, minimised at one field in one persistent launch (after the
-    autotuner picked the kernel instantiation and team split), against the
+    autotuner picked the kernel instantiation, team split and tile shape),
+    against the
     same problems minimised one after the other, in the precision form with
     the Jacobi and with the multigrid potential preconditioner."""
     import torch
@@ -915,7 +917,7 @@ def batch_mode(args, rank, local_rank):
         reset(0)
         batch = Batch(mags)
         bps, gamma, ms = batch.autotune(prm)
-        res["autotune"] = {"blocks_per_sm": bps, "gamma": gamma, "trial_ms": ms}
+        res["autotune"] = dict(batch.get_config(), trial_ms=ms)
         for k in (0, 1, 2):                               # warm-up field steps
             reset(k) if k == 0 else [m.set_field(wl.fields[k]) for m, wl in zip(mags, wls)]
             batch.minimize(prm)

@@ -194,6 +194,17 @@ int mm_amg_host_apply(int64_t n, const int64_t* row_ptr, const int32_t* col, con
                       int32_t n_vec, const double* r, double* z, int32_t* n_levels,
                       int64_t* rows, int32_t max_rows);
 
+/* Tile shape of the solver kernel's FP32 potential-solve products (no
+ * counterpart in the paper; the results differ only by rounding):
+ * rows_per_thread 1 or 2 (0 = default 2) -- SELL-32 rows each thread takes
+ * at once in the level-0 products with K_phi and the smoothed prolongation,
+ * two keeping twice the loads in flight; restrict_lanes 4, 8 or 16 (0 =
+ * default 8) -- lanes that share one row of a restriction P^T (levels whose
+ * rows average over 160 entries always take 32).  Kept by the context across
+ * mm_upload_mesh; takes effect at the next solver launch.  MM_ERR_ARG for
+ * other values. */
+int mm_set_tiles(mm_ctx* ctx, int32_t rows_per_thread, int32_t restrict_lanes);
+
 /* Magnetisation per node ([n_nodes][3]); normalised on entry (N m, Eq. opt2). */
 int mm_set_magnetization(mm_ctx* ctx, const double* m);
 int mm_get_magnetization(mm_ctx* ctx, double* m_out);
@@ -341,9 +352,20 @@ int mm_batch_minimize(mm_batch* b, const mm_params* p, mm_stats* stats_out);
  * round trip in between.  stats_out [n_steps][n] (may be NULL). */
 int mm_batch_demag_curve(mm_batch* b, int64_t n_steps, const double* fields,
                          const mm_params* p, mm_stats* stats_out);
-/* Time each kernel instantiation x team-split exponent on a short
- * minimisation (max_iter capped at 25) of the members' current states,
- * restoring the states after each trial, and keep the fastest. */
+/* Tile shape of every member in batch launches, as in mm_set_tiles (the
+ * members' own settings are not used by batch launches). */
+int mm_batch_set_tiles(mm_batch* b, int32_t rows_per_thread, int32_t restrict_lanes);
+/* The configuration batch launches use: kernel instantiation, team-split
+ * exponent, rows per thread and restriction lanes (defaults resolved).
+ * Any output may be NULL. */
+int mm_batch_get_config(const mm_batch* b, int32_t* blocks_per_sm, double* gamma,
+                        int32_t* rows_per_thread, int32_t* restrict_lanes);
+/* Time configurations on a short minimisation (max_iter capped at 25) of
+ * the members' current states, restoring the states after each trial, and
+ * keep the fastest: first the 3 kernel instantiations x 3 team-split
+ * exponents (0.5, 0.75, 1) at the default tile shape, then at the best of
+ * those the 6 tile shapes (rows per thread 2 or 1 x restriction lanes 8, 4
+ * or 16).  The chosen tile shape is read with mm_batch_get_config. */
 int mm_batch_autotune(mm_batch* b, const mm_params* p, int* chosen_blocks_per_sm,
                       double* chosen_gamma, double* best_ms);
 /* Device time (ms) of the last batch launch or curve. */

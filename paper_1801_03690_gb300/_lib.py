@@ -71,6 +71,7 @@ EXPORTS = {
     "mm_set_magnetization_dev": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mm_get_magnetization_dev": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mm_set_field": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mm_set_tiles": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "mm_minimize": (C.c_int, [C.c_void_p, C.POINTER(mm_params), C.POINTER(mm_stats)]),
     "mm_minimize_async": (C.c_int, [C.c_void_p, C.POINTER(mm_params)]),
     "mm_get_stats": (C.c_int, [C.c_void_p, C.POINTER(mm_stats)]),
@@ -93,6 +94,9 @@ EXPORTS = {
     "mm_batch_destroy": (None, [C.c_void_p]),
     "mm_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "mm_batch_config": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "mm_batch_set_tiles": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "mm_batch_get_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mm_batch_minimize": (C.c_int, [C.c_void_p, C.POINTER(mm_params), C.POINTER(mm_stats)]),
     "mm_batch_demag_curve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(mm_params),
                                        C.POINTER(mm_stats)]),

@@ -164,6 +164,11 @@ class Magnet:
         b = (C.c_double * 3)(*[float(x) for x in mu0h])
         self._check(self._lib.mm_set_field(self._h, b))
 
+    def set_tiles(self, rows_per_thread=0, restrict_lanes=0):
+        """Tile shape of the FP32 potential-solve products (0 = default:
+        two rows per thread, eight lanes per restriction row)."""
+        self._check(self._lib.mm_set_tiles(self._h, int(rows_per_thread), int(restrict_lanes)))
+
     # ------------------------------------------------------------ operations
     def minimize(self, params=None):
         p = (params or Params()).to_c()
@@ -358,6 +363,18 @@ class Batch:
 
     def config(self, blocks_per_sm=3, gamma=1.0):
         self._check(self._lib.mm_batch_config(self._h, int(blocks_per_sm), float(gamma)))
+
+    def set_tiles(self, rows_per_thread=0, restrict_lanes=0):
+        self._check(self._lib.mm_batch_set_tiles(self._h, int(rows_per_thread), int(restrict_lanes)))
+
+    def get_config(self):
+        """The configuration batch launches use (after autotune: the chosen one)."""
+        bps, rows, lanes = C.c_int32(), C.c_int32(), C.c_int32()
+        gamma = C.c_double()
+        self._check(self._lib.mm_batch_get_config(self._h, C.byref(bps), C.byref(gamma), C.byref(rows),
+                                                  C.byref(lanes)))
+        return {"blocks_per_sm": bps.value, "gamma": gamma.value, "rows_per_thread": rows.value,
+                "restrict_lanes": lanes.value}
 
     def minimize(self, params=None):
         p = (params or Params()).to_c()

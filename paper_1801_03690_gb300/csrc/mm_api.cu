@@ -112,6 +112,7 @@ struct mm_ctx {
     double field_T[3] = {0, 0, 0};
     std::vector<void*> allocs;            // device buffers of the mesh
     mm::Problem P{};
+    int tile_rows = 0, restrict_lanes = 0;   // mm_set_tiles (0 = default); kept across uploads
     mm::DevState* d_state = nullptr;      // device
     mm::DevState* h_state = nullptr;      // pinned host
     int* d_mag_nodes = nullptr;
@@ -170,6 +171,8 @@ void free_mesh(mm_ctx* ctx) {
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
     ctx->P = mm::Problem{};
+    ctx->P.tile_rows = ctx->tile_rows;
+    ctx->P.restrict_lanes = ctx->restrict_lanes;
     ctx->has_mesh = false;
     ctx->has_eval = false;
 }
@@ -1469,6 +1472,16 @@ int mm_amg_host_apply(int64_t n, const int64_t* row_ptr, const int32_t* col, con
     if (!ok) return MM_OK;
     for (int l = 0; l <= L && rows && l < max_rows; ++l) rows[l] = (l < L) ? H.lev[l].A.n : H.nco;
     for (int32_t v = 0; v < n_vec; ++v) amg_host_vcycle(H, 0, r + (size_t)v * n, z + (size_t)v * n);
+    return MM_OK;
+}
+
+int mm_set_tiles(mm_ctx* ctx, int32_t rows_per_thread, int32_t restrict_lanes) {
+    if (!ctx) return MM_ERR_ARG;
+    if (rows_per_thread < 0 || rows_per_thread > 2) return fail(ctx, MM_ERR_ARG, "rows_per_thread must be 0, 1 or 2");
+    if (restrict_lanes != 0 && restrict_lanes != 4 && restrict_lanes != 8 && restrict_lanes != 16)
+        return fail(ctx, MM_ERR_ARG, "restrict_lanes must be 0, 4, 8 or 16");
+    ctx->tile_rows = ctx->P.tile_rows = rows_per_thread;
+    ctx->restrict_lanes = ctx->P.restrict_lanes = restrict_lanes;
     return MM_OK;
 }
 

@@ -52,6 +52,7 @@ struct mm_batch {
     std::vector<int64_t> work;
     int variant = 3;
     double gamma = 1.0;
+    int tile_rows = 0, restrict_lanes = 0;   // tile shape of every member (0 = default)
     int blocks = 0;
     std::vector<int> team_first;
     std::string err;
@@ -137,6 +138,8 @@ int prepare(mm_batch* b, const mm::Params& prm) {
         mm::Problem q = *b->views[t].P;
         q.prm = prm;
         q.mode = mm::MODE_MINIMIZE;
+        q.tile_rows = b->tile_rows;
+        q.restrict_lanes = b->restrict_lanes;
         q.partials = b->d_part + 2 * (size_t)MM_MAXRED * b->team_first[t];
         q.bar = b->d_bar + (size_t)kBarWords * t;
         q.err = b->d_err + (size_t)kErrWords * t;
@@ -320,6 +323,26 @@ int mm_batch_config(mm_batch* b, int blocks_per_sm, double gamma) {
     return MM_OK;
 }
 
+int mm_batch_set_tiles(mm_batch* b, int32_t rows_per_thread, int32_t restrict_lanes) {
+    if (!b) return MM_ERR_ARG;
+    if (rows_per_thread < 0 || rows_per_thread > 2) return bfail(b, MM_ERR_ARG, "rows_per_thread must be 0, 1 or 2");
+    if (restrict_lanes != 0 && restrict_lanes != 4 && restrict_lanes != 8 && restrict_lanes != 16)
+        return bfail(b, MM_ERR_ARG, "restrict_lanes must be 0, 4, 8 or 16");
+    b->tile_rows = rows_per_thread;
+    b->restrict_lanes = restrict_lanes;
+    return MM_OK;
+}
+
+int mm_batch_get_config(const mm_batch* b, int32_t* blocks_per_sm, double* gamma, int32_t* rows_per_thread,
+                        int32_t* restrict_lanes) {
+    if (!b) return MM_ERR_ARG;
+    if (blocks_per_sm) *blocks_per_sm = b->variant;
+    if (gamma) *gamma = b->gamma;
+    if (rows_per_thread) *rows_per_thread = b->tile_rows == 1 ? 1 : 2;
+    if (restrict_lanes) *restrict_lanes = (b->restrict_lanes == 4 || b->restrict_lanes == 16) ? b->restrict_lanes : 8;
+    return MM_OK;
+}
+
 int mm_batch_minimize(mm_batch* b, const mm_params* p, mm_stats* stats_out) {
     if (!b) return MM_ERR_ARG;
     int rc;
@@ -462,46 +485,75 @@ int mm_batch_autotune(mm_batch* b, const mm_params* p, int* chosen_blocks_per_sm
         }
         return MM_OK;
     };
+    // One trial: the launch time of the current configuration (1e300 when it
+    // does not fit), the members' states restored afterwards.
+    auto trial = [&](double& ms) -> int {
+        ms = 1e300;
+        int r = prepare(b, prm);
+        if (r == MM_ERR_ARG) return MM_OK;   // too many problems for this grid
+        if (r) return r;
+        BK(cudaEventRecord(b->ev0, b->stream));
+        if ((r = enqueue_launch(b))) return r;
+        BK(cudaEventRecord(b->ev1, b->stream));
+        BK(cudaStreamSynchronize(b->stream));
+        if ((r = check_errors(b))) return r;
+        float t = 0.f;
+        BK(cudaEventElapsedTime(&t, b->ev0, b->ev1));
+        ms = t;
+        return restore();
+    };
+    // Stage 1: kernel instantiation x team split at the default tile shape;
+    // stage 2: the tile shape (rows per thread x restriction lanes) at the
+    // best of stage 1.
     const int variants[3] = {2, 3, 4};
     const double gammas[3] = {0.5, 0.75, 1.0};
+    const int rows[2] = {2, 1};
+    const int lanes[3] = {8, 4, 16};
     double best = 1e300;
-    int bv = b->variant;
+    int bv = b->variant, br = 0, bl = 0;
     double bg = b->gamma;
+    b->tile_rows = 0;
+    b->restrict_lanes = 0;
     for (int vi = 0; vi < 3; ++vi)
         for (int gi = 0; gi < 3; ++gi) {
             b->variant = variants[vi];
             b->gamma = gammas[gi];
-            if ((rc = prepare(b, prm)) == MM_ERR_ARG) continue;   // too many problems for this grid
-            if (rc) {
+            double ms;
+            if ((rc = trial(ms))) {
                 release();
                 return rc;
             }
-            BK(cudaEventRecord(b->ev0, b->stream));
-            if ((rc = enqueue_launch(b))) {
-                release();
-                return rc;
-            }
-            BK(cudaEventRecord(b->ev1, b->stream));
-            BK(cudaStreamSynchronize(b->stream));
-            if ((rc = check_errors(b))) {
-                release();
-                return rc;
-            }
-            float ms = 0.f;
-            BK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
             if (ms < best) {
                 best = ms;
                 bv = variants[vi];
                 bg = gammas[gi];
             }
-            if ((rc = restore())) {
-                release();
-                return rc;
-            }
         }
+    if (best < 1e300) {
+        b->variant = bv;
+        b->gamma = bg;
+        for (int ri = 0; ri < 2; ++ri)
+            for (int li = 0; li < 3; ++li) {
+                if (ri == 0 && li == 0) continue;   // the default shape, timed in stage 1
+                b->tile_rows = rows[ri];
+                b->restrict_lanes = lanes[li];
+                double ms;
+                if ((rc = trial(ms))) {
+                    release();
+                    return rc;
+                }
+                if (ms < best) {
+                    best = ms;
+                    br = rows[ri];
+                    bl = lanes[li];
+                }
+            }
+    }
     release();
     b->variant = bv;
     b->gamma = bg;
+    b->tile_rows = br;
+    b->restrict_lanes = bl;
     for (int t = 0; t < n; ++t) mm::ctx_refresh_state(b->ctxs[t]);
     if (chosen_blocks_per_sm) *chosen_blocks_per_sm = bv;
     if (chosen_gamma) *chosen_gamma = bg;

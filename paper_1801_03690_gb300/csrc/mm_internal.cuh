@@ -173,6 +173,12 @@ struct Problem {
     DevState* state;
     Params prm;
     int mode;
+    // tile shape of the level-0 FP32 products and of the restrictions
+    // (zero-initialised = the defaults): tile_rows 1 = one row per thread,
+    // else two; restrict_lanes 4 or 16 lanes per coarse row, else 8 (levels
+    // with wide rows always take a whole warp)
+    int tile_rows;
+    int restrict_lanes;
 };
 
 // Read-only view of a context for entry points defined outside mm_api.cu.

@@ -319,6 +319,35 @@ __device__ __forceinline__ void sell_dot_2rows(const long long* __restrict__ spt
     for (int r = t.rank * MM_BLOCK + (int)threadIdx.x, r2 = 0; r < (n); r += 2 * t.nb * MM_BLOCK) \
         if (const bool two = ((r2 = r + t.nb * MM_BLOCK) < (n)); true)
 
+// The FP32 products of level 0 (K_phi and the smoothed prolongation) over the
+// team's rows in the tile shape P.tile_rows selects; f(r, s, v) takes row r,
+// its sum s and v = pre(r), the row's vector operands, which pre loads before
+// the product's loads are issued: the vector loads then overlap the matrix
+// loads and the gathers instead of following them.  Both shapes visit a
+// thread's rows in the same order (r, r + stride, r + 2 stride, ...), so
+// per-thread sums f accumulates come out in the same order too.  pad_self:
+// lanes past a row's width gather x[r] (square matrices) rather than x[0].
+template <class Pre, class F>
+__device__ __forceinline__ void level0_products(const Problem& P, const Team& t, const long long* __restrict__ sptr,
+                                                const int* __restrict__ col, const float* __restrict__ val,
+                                                const float* x, int n, bool pad_self, Pre pre, F f) {
+    if (P.tile_rows != 1) {
+        ROWS2(r, r2, two, n) {
+            const auto v0 = pre(r);
+            const auto v1 = pre(two ? r2 : r);
+            float s0, s1;
+            sell_dot_2rows<8>(sptr, col, val, x, r, r2, two, pad_self ? r : 0, s0, s1);
+            f(r, s0, v0);
+            if (two) f(r2, s1, v1);
+        }
+    } else {
+        ROWS(r, n) {
+            const auto v0 = pre(r);
+            f(r, sell_dot<16, float>(sptr, col, val, x, r, pad_self ? r : 0), v0);
+        }
+    }
+}
+
 // ---- row kernels of the three operators of Eq. (energy) on the magnetic
 // graph, shared by the solver phases and the operator entry point.
 
@@ -571,9 +600,6 @@ __device__ __forceinline__ void dot2_merge(Dot2& d, float p, float s) {
 // entries gl, gl + G, ..., CH per pass with all of a pass's loads issued
 // before any gather, accumulates them compensated, and the group combines
 // its lanes with a G-lane xor reduction (every lane of the warp takes part).
-#ifndef MM_RESTRICT_G
-#define MM_RESTRICT_G 8
-#endif
 template <int G, int CH, class XF>
 __device__ __forceinline__ float group_csr_dot2(const long long* __restrict__ ptr, const int* __restrict__ col,
                                                 const float* __restrict__ val, XF x, int row, int gl) {
@@ -635,13 +661,15 @@ __device__ __forceinline__ void amg_restrict_g(const Problem& P, const Team& t, 
 
 // Levels with few, long restriction rows (the coarse end of the hierarchy:
 // hundreds of entries per row, a few hundred rows) take a whole warp per
-// row, the others a group of MM_RESTRICT_G lanes (measured on the 8.7 M-
-// unknown polycrystal: 8 lanes 190 us, 4 lanes 211, 16 lanes 225 for the
-// level-0 down phase).
+// row, the others a group of P.restrict_lanes lanes, 8 by default (measured
+// on the 8.7 M-unknown polycrystal: 8 lanes 190 us, 4 lanes 211, 16 lanes
+// 225 for the level-0 down phase).
 template <class XF>
 __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, const Level& V, int l, XF bx) {
     if (V.wide) amg_restrict_g<32>(P, t, V, l, bx);
-    else amg_restrict_g<MM_RESTRICT_G>(P, t, V, l, bx);
+    else if (P.restrict_lanes == 4) amg_restrict_g<4>(P, t, V, l, bx);
+    else if (P.restrict_lanes == 16) amg_restrict_g<16>(P, t, V, l, bx);
+    else amg_restrict_g<8>(P, t, V, l, bx);
 }
 
 // Down phase of level l; at level 0, b is the FP32 residual and x = omega
@@ -659,12 +687,8 @@ __device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
     if (l == 0) {
         // level 0 (K_phi, a handful of entries per row): two rows per thread
         // keep twice the loads in flight (+3.5% on the 8.7 M-unknown polycrystal)
-        ROWS2(r, r2, two, V.n) {
-            float s0, s1;
-            sell_dot_2rows<8>(V.sptr, V.col, V.val, x, r, r2, two, r, s0, s1);
-            V.rpre[r] = b[r] - s0;
-            if (two) V.rpre[r2] = b[r2] - s1;
-        }
+        level0_products(P, t, V.sptr, V.col, V.val, x, V.n, true, [&](int r) { return b[r]; },
+                        [&](int r, float s, float br) { V.rpre[r] = br - s; });
     } else {
         ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
     }
@@ -700,22 +724,24 @@ __device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
     const float* yc = (l + 1 == P.nlev) ? P.yco : P.lev[l + 1].y;
     const float* bv = (l == 0) ? P.pres32 : V.b;
     float acc[2] = {0.0f, 0.0f};
-    auto row = [&](int r, float s) {
+    // per row: b and omega D^-1 (b + rpre), loaded ahead of the product
+    auto pre = [&](int r) {
         const float b = bv[r];
-        const float y = V.omega * V.dinv[r] * (b + V.rpre[r]) + s;
+        return make_float2(b, V.omega * V.dinv[r] * (b + V.rpre[r]));
+    };
+    auto row = [&](int r, float s, float2 v) {
+        const float y = v.y + s;
         V.y[r] = y;
-        acc[0] += b * y;
-        acc[1] += b * b;
+        acc[0] += v.x * y;
+        acc[1] += v.x * v.x;
     };
     if (l == 0) {
-        ROWS2(r, r2, two, V.n) {
-            float s0, s1;
-            sell_dot_2rows<8>(V.u_sptr, V.u_col, V.u_val, yc, r, r2, two, 0, s0, s1);
-            row(r, s0);
-            if (two) row(r2, s1);
-        }
+        level0_products(P, t, V.u_sptr, V.u_col, V.u_val, yc, V.n, false, pre, row);
     } else {
-        ROWS(r, V.n) row(r, sell_dot<16, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0));
+        ROWS(r, V.n) {
+            const float2 v = pre(r);
+            row(r, sell_dot<16, float>(V.u_sptr, V.u_col, V.u_val, yc, r, 0), v);
+        }
     }
     if (l > 0) return team_sync(t);
     double out[2];
@@ -779,19 +805,17 @@ __device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
     double out[1];
     const bool first = (beta == 0.0f);
     const float* z = P.pprec32;
-    auto row = [&](int p, float s) {
-        const float dn = first ? z[p] : z[p] + beta * P.pdir32[p];
-        const float qn = first ? s : s + beta * P.pq32[p];
-        P.pdir32[p] = dn;
-        P.pq32[p] = qn;
-        acc[0] += dn * qn;
+    // per row: the new direction z + beta d and beta q, loaded ahead of the product
+    auto pre = [&](int p) {
+        return first ? make_float2(z[p], 0.0f) : make_float2(z[p] + beta * P.pdir32[p], beta * P.pq32[p]);
     };
-    ROWS2(p, p2, two, P.nphi) {
-        float s0, s1;
-        sell_dot_2rows<8>(P.p_sptr, P.p_col, P.Kp32, z, p, p2, two, p, s0, s1);
-        row(p, s0);
-        if (two) row(p2, s1);
-    }
+    auto row = [&](int p, float s, float2 v) {
+        const float qn = s + v.y;
+        P.pdir32[p] = v.x;
+        P.pq32[p] = qn;
+        acc[0] += v.x * qn;
+    };
+    level0_products(P, t, P.p_sptr, P.p_col, P.Kp32, z, P.nphi, true, pre, row);
     if (!team_sum_f32<1>(t, acc, out)) return false;
     dq = out[0];
     return true;

@@ -131,3 +131,40 @@ def test_amg_two_level_minimize_matches_oracle(lib):
     assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
     assert np.abs(m - r.m).max() < 1e-5
     mag.close()
+
+
+def test_tile_shapes_match_oracle(lib):
+    """Every tile shape of the FP32 products (rows per thread 1 or 2 x
+    restriction lanes 4, 8 or 16) reaches the oracle's minimum on the
+    two-level cube (energy 1e-8, max nodal |dm| 1e-5); the shapes change only
+    the rounding of the potential solve, so they agree with one another to
+    the potential tolerance's reach (energy 1e-10, m 1e-6)."""
+    Magnet, Params, MMError = lib
+    wl = synth.hard_cube(n_mag=24)
+    P = fem.assemble_workload(wl)
+    b = wl.fields[3]
+    prm = Params(jmax=4, precision=1, amg=1, inner_tol=1e-3, poisson_tol=1e-12)
+    r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=4, poisson="cg", poisson_tol=1e-12))
+    mag = Magnet(device=0)
+    mag.upload_workload(wl)
+    with pytest.raises(MMError):
+        mag.set_tiles(3, 8)
+    with pytest.raises(MMError):
+        mag.set_tiles(2, 12)
+    out = {}
+    for rows in (2, 1):
+        for lanes in (8, 4, 16):
+            mag.set_tiles(rows, lanes)
+            mag.set_magnetization(wl.m0)
+            mag.set_field(b)
+            st = mag.minimize(prm)
+            out[rows, lanes] = (st, mag.get_magnetization()[P.mag_nodes])
+    mag.close()
+    s0, m0 = out[2, 8]
+    for key, (st, m) in out.items():
+        assert st["status"] == "ok", key
+        assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8), key
+        assert np.abs(m - r.m).max() < 1e-5, key
+        assert st["F"] == pytest.approx(s0["F"], rel=1e-10), key
+        assert np.abs(m - m0).max() < 1e-6, key

@@ -101,6 +101,9 @@ def test_batch_autotune_keeps_results():
     batch = Batch(mags)
     bps, gamma, ms = batch.autotune(prm)
     assert bps in (2, 3, 4) and gamma in (0.5, 0.75, 1.0) and ms > 0
+    cfg = batch.get_config()
+    assert cfg["blocks_per_sm"] == bps and cfg["gamma"] == gamma
+    assert cfg["rows_per_thread"] in (1, 2) and cfg["restrict_lanes"] in (4, 8, 16)
     for m, b0 in zip(mags, before):                  # states restored
         np.testing.assert_array_equal(m.get_magnetization(), b0)
     sts = batch.minimize(prm)
