@@ -86,6 +86,16 @@ def workload_desc(name, wl, sizes=None):
 
 
 # ------------------------------------------------------------ algorithmic bytes
+def model_sizes(mag):
+    """Sizes the byte model needs: the mesh's (mm_sizes) and the matrix bytes
+    of one product with the FP32 K_phi in its uploaded layout."""
+    sz = mag.sizes()
+    k = mag.k32_layout()
+    sz["k32_bytes"] = k["matrix_bytes"]
+    sz["k32_table_slice_frac"] = k["table_slices"] / max(k["slices"], 1)
+    return sz
+
+
 def form_params(form, theta_max=0.1):
     """Parameters of the three forms of a field step: 0 plain FP64
     (Jacobi-preconditioned potential solve, the paper's method in FP64), 1
@@ -100,17 +110,20 @@ def form_params(form, theta_max=0.1):
                   poisson_sched=1, theta_max=theta_max)
 
 
-def vcycle_bytes(amg):
+def vcycle_bytes(amg, k32_bytes=None):
     """Bytes of one multigrid V-cycle (levels l < L smoothed, L dense):
       down_l  8 nnz_A_l + 12 n_l + 8 nnz_P_l + 12 n_{l+1} (4 n_L at the last)
-              (A and P^T val+col; x, b read, rpre written; b, x of l+1 written)
+              (A and P^T val+col; x, b read, rpre written; b, x of l+1 written;
+              at level 0, A is the FP32 K_phi: k32_bytes for the matrix when
+              given, the layout's own count)
       dense   4 n_L^2 + 8 n_L
       up_l    8 nnz_U_l + 4 n_{l+1} + 16 n_l (U; y_{l+1}; b, rpre, diag^-1 -> y)"""
     L = len(amg) - 1
     tot = 4 * amg[L]["nnz_a"] + 8 * amg[L]["rows"]
     for l in range(L):
         n, nc = amg[l]["rows"], amg[l + 1]["rows"]
-        tot += 8 * amg[l]["nnz_a"] + 12 * n + 8 * amg[l]["nnz_p"] + (4 if l + 1 == L else 12) * nc
+        a_bytes = k32_bytes if (l == 0 and k32_bytes is not None) else 8 * amg[l]["nnz_a"]
+        tot += a_bytes + 12 * n + 8 * amg[l]["nnz_p"] + (4 if l + 1 == L else 12) * nc
         tot += 8 * amg[l]["nnz_u"] + 4 * nc + 16 * n
     return tot
 
@@ -134,12 +147,16 @@ def alg_bytes(st, sz, amg=None):
       inner step (li)       12 nnz_mag + 352 n_mag  (H product + update)
       per iteration (nli+1) 272 n_mag               (inner set-up + direction)
     nnz_phi is the stored potential stiffness (without the rounding residues
-    the upload drops).
+    the upload drops).  The FP32 products' 8 nnz_phi (val+col) become
+    sz["k32_bytes"] when given: the matrix bytes of the FP32 K_phi's own
+    layout (slices with an offset table store values only).
     """
     nphi, nm = sz["n_phi"], sz["n_mag"]
     nzp, nzm = sz["nnz_phi"], sz["nnz_mag"]
+    kb = sz.get("k32_bytes")
+    k32 = 8 * nzp if kb is None else kb
     per_pcg = 12 * nzp + 96 * nphi
-    per_pcg32 = 8 * nzp + 52 * nphi          # FP32 step: val+col 8 B/nnz; 13 FP32 vector passes
+    per_pcg32 = k32 + 52 * nphi              # FP32 step: the matrix; 13 FP32 vector passes
     per_refine = 12 * nzp + 60 * nphi        # FP64 residual product + FP32 set-up
     per_eval = 12 * nzp + 64 * nzm + 48 * nphi + 208 * nm
     per_trial = 112 * nm
@@ -147,8 +164,8 @@ def alg_bytes(st, sz, amg=None):
     per_iter = 272 * nm
     mr = st.get("mr", 0)
     if amg:
-        vc = vcycle_bytes(amg)
-        per_pcg32 = 8 * nzp + 20 * nphi + 32 * nphi + vc
+        vc = vcycle_bytes(amg, kb)
+        per_pcg32 = k32 + 20 * nphi + 32 * nphi + vc
         per_refine += vc
     steps = (st["mi"] - mr) * per_pcg32 + mr * per_refine if mr else st["mi"] * per_pcg
     return (steps + st["evals"] * per_eval + max(st["evals"] - 1, 0) * per_trial
@@ -444,7 +461,7 @@ def main():
     t0 = time.perf_counter()
     mag.upload_workload(wl)
     t_up = time.perf_counter() - t0
-    sz = mag.sizes()
+    sz = model_sizes(mag)
     stream = torch.cuda.ExternalStream(mag.stream, device=torch.device("cuda", local_rank))
     ranks = Ranks(world, torch.device("cuda", local_rank))
     barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
@@ -854,7 +871,7 @@ def scaling_mode(args, rank, local_rank):
         wl = synth.hard_cube(n_mag=n)
         mag = Magnet(device=local_rank)
         mag.upload_workload(wl)
-        sz = mag.sizes()
+        sz = model_sizes(mag)
         lv = mag.amg_info() if prm.amg else None
         mag.set_magnetization(wl.m0)
         for k in range(3):

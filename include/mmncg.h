@@ -176,6 +176,30 @@ int mm_sizes(const mm_ctx* ctx, int64_t* n_mag, int64_t* n_phi,
 int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nnz_a,
                 int64_t* nnz_u, int64_t* nnz_p, int32_t max_entries);
 
+/* Layout of the FP32 copy of K_phi the precision form streams (no
+ * counterpart in the paper): *slices SELL-32 slices, *table_slices of them
+ * with an offset table -- every row of such a slice couples to its own
+ * index plus one of at most 8 offsets shared by the slice (the stencil of a
+ * rectilinear lattice), so the slice stores values only -- and
+ * *matrix_bytes, the bytes one FP32 product loads for the matrix (4 per
+ * stored value in table slices, 8 per nonzero elsewhere, 32 per slice for
+ * the table).  Any output may be NULL; MM_ERR_STATE without a mesh. */
+int mm_k32_layout_info(const mm_ctx* ctx, int64_t* slices, int64_t* table_slices,
+                       int64_t* matrix_bytes);
+
+/* Host only (no GPU, no context): the FP32 layout that mm_upload_mesh
+ * builds for K_phi (see mm_k32_layout_info), built for the symmetric matrix
+ * A given in CSR (row_ptr [n+1], col [nnz], val [nnz], FP64; the caller
+ * keeps ownership; A without its rounding residues, as upload stores it),
+ * and applied in FP32 to x [n], writing y [n] = A x: every row summed over
+ * its stored entries in the order the solver kernel sums them.  This is the
+ * layout the kernel reads, exposed so that it can be checked without a GPU.
+ * *table_slices and *matrix_bytes as in mm_k32_layout_info (may be NULL).
+ * MM_ERR_ARG for null pointers, n < 1, decreasing row_ptr or a column
+ * outside [0, n). */
+int mm_k32_host_apply(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                      const float* x, float* y, int64_t* table_slices, int64_t* matrix_bytes);
+
 /* Host only (no GPU, no context): build the multigrid hierarchy that
  * mm_upload_mesh builds for K_phi, for the symmetric positive definite
  * matrix A given in CSR (row_ptr [n+1], col [nnz], val [nnz], FP64; the

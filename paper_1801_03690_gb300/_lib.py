@@ -62,6 +62,9 @@ EXPORTS = {
     "mm_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int64)] * 4),
     "mm_amg_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                               C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
+    "mm_k32_host_apply": (C.c_int, [C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mm_amg_host_apply": (C.c_int, [C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
@@ -72,6 +75,8 @@ EXPORTS = {
     "mm_get_magnetization_dev": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mm_set_field": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mm_set_tiles": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "mm_k32_layout_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]),
     "mm_minimize": (C.c_int, [C.c_void_p, C.POINTER(mm_params), C.POINTER(mm_stats)]),
     "mm_minimize_async": (C.c_int, [C.c_void_p, C.POINTER(mm_params)]),
     "mm_get_stats": (C.c_int, [C.c_void_p, C.POINTER(mm_stats)]),

@@ -123,6 +123,14 @@ class Magnet:
         self._check(self._lib.mm_sizes(self._h, *[C.byref(x) for x in v]))
         return {"n_mag": v[0].value, "n_phi": v[1].value, "nnz_mag": v[2].value, "nnz_phi": v[3].value}
 
+    def k32_layout(self):
+        """Layout of the FP32 K_phi the precision form streams: SELL-32
+        slices, slices with an offset table (values only) and the matrix
+        bytes of one product."""
+        v = [C.c_int64() for _ in range(3)]
+        self._check(self._lib.mm_k32_layout_info(self._h, *[C.byref(x) for x in v]))
+        return {"slices": v[0].value, "table_slices": v[1].value, "matrix_bytes": v[2].value}
+
     def amg_levels(self):
         """Rows of every level of the potential solve's multigrid hierarchy,
         finest first, coarsest (dense) last; [] when there is none."""
@@ -330,6 +338,28 @@ def amg_host_apply(indptr, indices, data, R):
     if nl.value == 0:
         return None, []
     return Z, [int(rows[l]) for l in range(nl.value + 1)]
+
+
+def k32_host_apply(indptr, indices, data, x):
+    """The FP32 layout of K_phi that mm_upload_mesh builds, built on the host
+    (no GPU needed) for the matrix in CSR form and applied in FP32 to x.
+    Returns (y, slices with an offset table, matrix bytes of one product)."""
+    lib = L.load()
+    ip = np.ascontiguousarray(indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    dv = np.ascontiguousarray(data, dtype=np.float64)
+    n = len(ip) - 1
+    xv = np.ascontiguousarray(x, dtype=np.float32)
+    if xv.shape != (n,):
+        raise ValueError("x must have n entries")
+    y = np.zeros(n, dtype=np.float32)
+    tabs, nbytes = C.c_int64(), C.c_int64()
+    rc = lib.mm_k32_host_apply(n, ip.ctypes.data_as(C.POINTER(C.c_int64)), ix.ctypes.data_as(C.POINTER(C.c_int32)),
+                               dv.ctypes.data_as(C.POINTER(C.c_double)), xv.ctypes.data_as(C.POINTER(C.c_float)),
+                               y.ctypes.data_as(C.POINTER(C.c_float)), C.byref(tabs), C.byref(nbytes))
+    if rc != 0:
+        raise MMError(rc, "mm_k32_host_apply rejected its arguments")
+    return y, tabs.value, nbytes.value
 
 
 class Batch:

@@ -113,6 +113,7 @@ struct mm_ctx {
     std::vector<void*> allocs;            // device buffers of the mesh
     mm::Problem P{};
     int tile_rows = 0, restrict_lanes = 0;   // mm_set_tiles (0 = default); kept across uploads
+    long long k32_slices = 0, k32_table_slices = 0, k32_bytes = 0;   // FP32 K_phi layout
     mm::DevState* d_state = nullptr;      // device
     mm::DevState* h_state = nullptr;      // pinned host
     int* d_mag_nodes = nullptr;
@@ -410,6 +411,97 @@ void csr_to_sell(const HostCsr& A, std::vector<long long>& sptr, std::vector<int
     }
 }
 
+// The FP32 copy of K_phi in SELL-32 with slice offset tables (the device
+// reads it as Problem::k_sptr / k_col / k_tab / Kp32).  A slice whose rows
+// couple, all together, to at most 8 distinct offsets c - r (on a
+// rectilinear Kuhn lattice: the diagonal and the six axis neighbours), with
+// r + offset a row of the matrix for every row r of the slice and every
+// offset, gets those offsets in ascending order as its table; each of its
+// rows stores one value per offset (0 where the row has no such coupling),
+// so a product loads no columns there.  Rows are column-sorted (the output of
+// prune_noise), so a table row lists the row's couplings in column order
+// with zeros between them and its sums equal those of the plain layout.
+// Other slices keep plain SELL-32 columns and MM_NO_TAB in table entry 0.
+struct K32Layout {
+    std::vector<long long> sptr;
+    std::vector<int> col;
+    std::vector<float> val;
+    std::vector<int> tab;          // [slices][8]
+    long long table_slices = 0;
+    long long bytes = 0;           // matrix bytes one product loads
+};
+
+K32Layout k32_layout(const HostCsr& K) {
+    K32Layout L;
+    const long long n = K.n, ns = (n + 31) / 32;
+    L.sptr.assign(ns + 1, 0);
+    L.tab.assign(ns * 8, 0);
+    std::vector<char> has_tab(ns, 0);
+    std::vector<int> D;
+    for (long long s = 0; s < ns; ++s) {
+        const long long r0 = 32 * s, r1 = std::min(n, r0 + 32);
+        long long wmax = 0;
+        for (long long r = r0; r < r1; ++r) wmax = std::max(wmax, K.ptr[r + 1] - K.ptr[r]);
+        bool ok = true;
+        D.clear();
+        for (long long r = r0; r < r1 && ok; ++r) {
+            for (long long e = K.ptr[r]; e < K.ptr[r + 1]; ++e) {
+                const int d = (int)(K.col[e] - r);
+                if (std::find(D.begin(), D.end(), d) == D.end()) {
+                    if (D.size() == 8) {
+                        ok = false;
+                        break;
+                    }
+                    D.push_back(d);
+                }
+            }
+        }
+        if (ok) {
+            std::sort(D.begin(), D.end());
+            for (long long r = r0; r < r1 && ok; ++r)
+                for (int d : D)
+                    if (r + d < 0 || r + d >= n) ok = false;
+        }
+        has_tab[s] = ok;
+        const long long w = ok ? (long long)D.size() : wmax;
+        L.sptr[s + 1] = L.sptr[s] + 32 * w;
+        if (ok) {
+            for (size_t k = 0; k < D.size(); ++k) L.tab[s * 8 + k] = D[k];
+            ++L.table_slices;
+            L.bytes += 4 * w * (r1 - r0) + 32;
+        } else {
+            L.tab[s * 8] = MM_NO_TAB;
+            L.bytes += 8 * (K.ptr[r1] - K.ptr[r0]) + 32;
+        }
+    }
+    L.col.assign(L.sptr[ns], 0);
+    L.val.assign(L.sptr[ns], 0.0f);
+    for (long long s = 0; s < ns; ++s) {
+        const long long w = (L.sptr[s + 1] - L.sptr[s]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const long long r = 32 * s + l;
+            const long long b = r < n ? K.ptr[r] : 0, e = r < n ? K.ptr[r + 1] : 0;
+            long long q = b;
+            for (long long k = 0; k < w; ++k) {
+                const long long x = L.sptr[s] + 32 * k + l;
+                if (r >= n) {
+                    L.col[x] = 0;                            // past the last row: never read
+                } else if (has_tab[s]) {
+                    const long long c = r + L.tab[s * 8 + k];
+                    L.col[x] = (int)c;
+                    if (q < e && K.col[q] == c) L.val[x] = (float)K.val[q++];
+                } else if (q < e) {
+                    L.col[x] = K.col[q];
+                    L.val[x] = (float)K.val[q++];
+                } else {
+                    L.col[x] = (int)r;                       // padding: column r, value 0
+                }
+            }
+        }
+    }
+    return L;
+}
+
 // Entries that are zero in exact arithmetic but not in floating point.
 // On a rectilinear (uniform or graded) Kuhn lattice the P1 Laplacian
 // couples a node only to its six axis neighbours: the couplings along face
@@ -675,10 +767,12 @@ int build_hierarchy(mm_ctx* ctx, mm::Problem& P, HostCsr A) {
         V.nc = h.U.m;
         V.omega = (float)h.omega;
         V.wide = (h.Pt.n > 0 && (double)h.Pt.col.size() / h.Pt.n > 160.0) ? 1 : 0;
+        V.tab = nullptr;
         if (l == 0) {
-            V.sptr = P.p_sptr;
-            V.col = P.p_col;
+            V.sptr = P.k_sptr;
+            V.col = P.k_col;
             V.val = P.Kp32;
+            V.tab = P.k_tab;
             V.dinv = P.dinvP32;
             V.b = nullptr;
             V.x = nullptr;
@@ -1264,8 +1358,10 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
             Kfull.ptr[r + 1] = (long long)Kfull.col.size();
         }
     }
+    K32Layout K32;
     {
         const HostCsr Kpr = prune_noise(Kfull);
+        K32 = k32_layout(Kpr);
         std::vector<double> v;
         csr_to_sell(Kpr, p_sptr, p_col, v);
         dfree(ctx, d_psp);
@@ -1316,13 +1412,24 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     if ((rc = dalloc(ctx, &P.pq, nphi))) return rc;
     {
         float *k32, *d32;
-        if ((rc = dalloc(ctx, &k32, nnzp))) return rc;
+        long long* ksp;
+        int *kcol, *ktab;
+        if ((rc = upload(ctx, &ksp, K32.sptr.data(), K32.sptr.size()))) return rc;
+        if ((rc = upload(ctx, &kcol, K32.col.data(), K32.col.size()))) return rc;
+        if ((rc = upload(ctx, &ktab, K32.tab.data(), K32.tab.size()))) return rc;
+        if ((rc = upload(ctx, &k32, K32.val.data(), K32.val.size()))) return rc;
         if ((rc = dalloc(ctx, &d32, nphi))) return rc;
-        k_to_f32<<<nblk(nnzp), 256, 0, ctx->stream>>>(nnzp, Kp, k32);
         k_to_f32<<<nblk(nphi), 256, 0, ctx->stream>>>(nphi, dinvP, d32);
         CK_CUDA(cudaGetLastError());
+        P.k_sptr = ksp;
+        P.k_col = kcol;
+        P.k_tab = ktab;
         P.Kp32 = k32;
         P.dinvP32 = d32;
+        ctx->k32_slices = (long long)K32.sptr.size() - 1;
+        ctx->k32_table_slices = K32.table_slices;
+        ctx->k32_bytes = K32.bytes;
+        K32 = K32Layout{};
         if ((rc = dalloc(ctx, &P.pres32, nphi))) return rc;
         if ((rc = dalloc(ctx, &P.pprec32, nphi))) return rc;
         if ((rc = dalloc(ctx, &P.pdir32, nphi))) return rc;
@@ -1443,6 +1550,49 @@ int mm_amg_info(const mm_ctx* ctx, int32_t* n_levels, int64_t* rows, int64_t* nn
         if (nnz_a) nnz_a[l] = ctx->amg_nnz_a[l];
         if (nnz_u && l < P.nlev) nnz_u[l] = ctx->amg_nnz_u[l];
         if (nnz_p && l < P.nlev) nnz_p[l] = ctx->amg_nnz_p[l];
+    }
+    return MM_OK;
+}
+
+int mm_k32_layout_info(const mm_ctx* ctx, int64_t* slices, int64_t* table_slices, int64_t* matrix_bytes) {
+    if (!ctx || !ctx->has_mesh) return MM_ERR_STATE;
+    if (slices) *slices = ctx->k32_slices;
+    if (table_slices) *table_slices = ctx->k32_table_slices;
+    if (matrix_bytes) *matrix_bytes = ctx->k32_bytes;
+    return MM_OK;
+}
+
+int mm_k32_host_apply(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, const float* x,
+                      float* y, int64_t* table_slices, int64_t* matrix_bytes) {
+    if (n < 1 || n > INT32_MAX || !row_ptr || !col || !val || !x || !y) return MM_ERR_ARG;
+    if (row_ptr[0] != 0) return MM_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return MM_ERR_ARG;
+    HostCsr A;
+    A.n = A.m = (int)n;
+    A.ptr.assign(row_ptr, row_ptr + n + 1);
+    const long long nnz = A.ptr[n];
+    A.col.resize(nnz);
+    A.val.resize(nnz);
+    for (long long e = 0; e < nnz; ++e) {
+        if (col[e] < 0 || col[e] >= n) return MM_ERR_ARG;
+        A.col[e] = col[e];
+        A.val[e] = val[e];
+    }
+    const K32Layout L = k32_layout(prune_noise(A));
+    if (table_slices) *table_slices = L.table_slices;
+    if (matrix_bytes) *matrix_bytes = L.bytes;
+    // the device's entry order: entry k of row r at sptr[s] + 32 k + (r % 32)
+    for (long long r = 0; r < n; ++r) {
+        const long long s = r / 32, w = (L.sptr[s + 1] - L.sptr[s]) / 32;
+        const bool tab = L.tab[s * 8] != MM_NO_TAB;
+        float acc = 0.0f;
+        for (long long k = 0; k < w; ++k) {
+            const long long e = L.sptr[s] + 32 * k + (r % 32);
+            const long long c = tab ? r + L.tab[s * 8 + k] : L.col[e];
+            acc += L.val[e] * x[c];
+        }
+        y[r] = acc;
     }
     return MM_OK;
 }

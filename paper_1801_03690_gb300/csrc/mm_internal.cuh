@@ -86,6 +86,9 @@ struct DevState {
 // residual, coarse correction and post-smoothing with the same damped
 // Jacobi step: a symmetric operator (P^T rpre = U^T b).  Operators are
 // FP32, SELL-32 except P^T (CSR).
+// Entry 0 of a slice offset table that marks a slice with a column array.
+#define MM_NO_TAB (-2147483647 - 1)
+
 struct Level {
     int n;                   // rows of this level
     int nc;                  // rows of the next coarser level
@@ -94,6 +97,7 @@ struct Level {
     const long long* sptr;   // A_l (level 0: the FP32 copy of K_phi)
     const int* col;
     const float* val;
+    const int* tab;          // level 0: the slice offset tables of K_phi (k_tab)
     const long long* u_sptr; // U (n rows, nc columns)
     const int* u_col;
     const float* u_val;
@@ -149,7 +153,14 @@ struct Problem {
     double* pprec;           // [nphi] Jacobi-preconditioned residual
     double* pdir[2];         // [nphi] direction (double buffer)
     double* pq;              // [nphi] K_phi * direction
-    // precision form: FP32 copies of K_phi and diag^-1, FP32 work vectors
+    // precision form: FP32 copies of K_phi and diag^-1, FP32 work vectors.
+    // The FP32 K_phi has a SELL-32 layout of its own (k_sptr, k_col) with a
+    // table of 8 column offsets per slice (k_tab): in a slice whose table
+    // does not start with MM_NO_TAB, entry k of row r is column r + tab[k]
+    // and k_col is not read (lattice stencils); other slices use k_col.
+    const long long* k_sptr;
+    const int* k_col;
+    const int* k_tab;        // [slices][8], 32-byte aligned rows
     const float* Kp32;
     const float* dinvP32;
     float* pres32;           // [nphi] residual of the correction equation

@@ -314,6 +314,67 @@ __device__ __forceinline__ void sell_dot_2rows(const long long* __restrict__ spt
     }
 }
 
+// The offset table of the slice of row r (MM_NO_TAB in entry 0: the slice
+// keeps its column array), two 16-byte loads that every lane of the warp
+// makes at the same address.
+struct SliceTab {
+    int d[8];
+};
+__device__ __forceinline__ SliceTab slice_tab(const int* __restrict__ tab, int r) {
+    const int4* t4 = reinterpret_cast<const int4*>(tab) + 2 * (r >> 5);
+    const int4 a = __ldg(t4), b = __ldg(t4 + 1);
+    return {{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w}};
+}
+
+// sell_dot_2rows for the FP32 K_phi layout with slice offset tables: when
+// both rows' slices have a table (at most 8 entries per row), entry u of row
+// r is column r + tab[u] and only the values are loaded; otherwise both rows
+// go through sell_dot_2rows on the layout's columns.  The entries of a table
+// slice are the row's couplings in column order with zeros for the offsets
+// it lacks, so the sums are those of the plain layout.  Square matrices
+// only (lanes past a row's width read x[r0]).
+__device__ __forceinline__ void sell_dot_2rows_tab(const long long* __restrict__ sptr, const int* __restrict__ col,
+                                                   const float* __restrict__ val, const int* __restrict__ tab,
+                                                   const float* x, int r0, int r1, bool two, float& s0, float& s1) {
+    const SliceTab ta = slice_tab(tab, r0);
+    const SliceTab tb = slice_tab(tab, two ? r1 : r0);
+    if (ta.d[0] == MM_NO_TAB || tb.d[0] == MM_NO_TAB) {
+        sell_dot_2rows<8>(sptr, col, val, x, r0, r1, two, r0, s0, s1);
+        return;
+    }
+    const Row A = sell_row(sptr, r0);
+    const Row B = two ? sell_row(sptr, r1) : Row{0, 0};
+    float v0[8], v1[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        v0[u] = u < A.width ? __ldcs(val + A.base + 32ll * u) : 0.0f;
+        v1[u] = u < B.width ? __ldcs(val + B.base + 32ll * u) : 0.0f;
+    }
+    s0 = 0.0f;
+    s1 = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        s0 += v0[u] * x[u < A.width ? r0 + ta.d[u] : r0];
+        s1 += v1[u] * x[u < B.width ? r1 + tb.d[u] : r0];
+    }
+}
+
+// One row of the same layout (sell_dot's one-row form, 16 entries per chunk).
+__device__ __forceinline__ float sell_dot_tab(const long long* __restrict__ sptr, const int* __restrict__ col,
+                                              const float* __restrict__ val, const int* __restrict__ tab,
+                                              const float* x, int r) {
+    const SliceTab ta = slice_tab(tab, r);
+    if (ta.d[0] == MM_NO_TAB) return sell_dot<16, float>(sptr, col, val, x, r, r);
+    const Row A = sell_row(sptr, r);
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = u < A.width ? __ldcs(val + A.base + 32ll * u) : 0.0f;
+    float s = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u] * x[u < A.width ? r + ta.d[u] : r];
+    return s;
+}
+
 // Grid-stride loop over row pairs (r, r2 = r + team stride); two: r2 < n.
 #define ROWS2(r, r2, two, n)                                                                     \
     for (int r = t.rank * MM_BLOCK + (int)threadIdx.x, r2 = 0; r < (n); r += 2 * t.nb * MM_BLOCK) \
@@ -325,25 +386,30 @@ __device__ __forceinline__ void sell_dot_2rows(const long long* __restrict__ spt
 // the product's loads are issued: the vector loads then overlap the matrix
 // loads and the gathers instead of following them.  Both shapes visit a
 // thread's rows in the same order (r, r + stride, r + 2 stride, ...), so
-// per-thread sums f accumulates come out in the same order too.  pad_self:
-// lanes past a row's width gather x[r] (square matrices) rather than x[0].
+// per-thread sums f accumulates come out in the same order too.  tab: the
+// slice offset tables of the FP32 K_phi (nullptr for other matrices).
+// pad_self: lanes past a row's width gather x[r] (square matrices) rather
+// than x[0].
 template <class Pre, class F>
 __device__ __forceinline__ void level0_products(const Problem& P, const Team& t, const long long* __restrict__ sptr,
                                                 const int* __restrict__ col, const float* __restrict__ val,
-                                                const float* x, int n, bool pad_self, Pre pre, F f) {
+                                                const int* __restrict__ tab, const float* x, int n, bool pad_self,
+                                                Pre pre, F f) {
     if (P.tile_rows != 1) {
         ROWS2(r, r2, two, n) {
             const auto v0 = pre(r);
             const auto v1 = pre(two ? r2 : r);
             float s0, s1;
-            sell_dot_2rows<8>(sptr, col, val, x, r, r2, two, pad_self ? r : 0, s0, s1);
+            if (tab) sell_dot_2rows_tab(sptr, col, val, tab, x, r, r2, two, s0, s1);
+            else sell_dot_2rows<8>(sptr, col, val, x, r, r2, two, pad_self ? r : 0, s0, s1);
             f(r, s0, v0);
             if (two) f(r2, s1, v1);
         }
     } else {
         ROWS(r, n) {
             const auto v0 = pre(r);
-            f(r, sell_dot<16, float>(sptr, col, val, x, r, pad_self ? r : 0), v0);
+            f(r, tab ? sell_dot_tab(sptr, col, val, tab, x, r) : sell_dot<16, float>(sptr, col, val, x, r, pad_self ? r : 0),
+              v0);
         }
     }
 }
@@ -678,19 +744,24 @@ __device__ __forceinline__ void amg_restrict(const Problem& P, const Team& t, co
 // half the entries of U^T (U^T b, the same vector, needs no barrier:
 // measured on the 8.7 M-unknown polycrystal, the U^T restriction took 205
 // of the phase's 323 us).
+// rpre = b - A x on the rows of level 0 (K_phi, a handful of entries per
+// row), a function of its own so that its registers are allocated apart
+// from the restriction's.
+__device__ __noinline__ void amg_down0_rows(const Problem& P, const Team& t) {
+    const Level& V = P.lev[0];
+    const float* b = P.pres32;
+    level0_products(P, t, V.sptr, V.col, V.val, V.tab, P.amg_x0, V.n, true, [&](int r) { return b[r]; },
+                    [&](int r, float s, float br) { V.rpre[r] = br - s; });
+}
+
 __device__ __noinline__ bool ph_amg_down(Ctx& C, int l) {
     const Problem& P = *C.P;
     Team& t = C.t;
     const Level& V = P.lev[l];
-    const float* b = (l == 0) ? P.pres32 : V.b;
-    const float* x = (l == 0) ? P.amg_x0 : V.x;
     if (l == 0) {
-        // level 0 (K_phi, a handful of entries per row): two rows per thread
-        // keep twice the loads in flight (+3.5% on the 8.7 M-unknown polycrystal)
-        level0_products(P, t, V.sptr, V.col, V.val, x, V.n, true, [&](int r) { return b[r]; },
-                        [&](int r, float s, float br) { V.rpre[r] = br - s; });
+        amg_down0_rows(P, t);
     } else {
-        ROWS(r, V.n) V.rpre[r] = b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, x, r);
+        ROWS(r, V.n) V.rpre[r] = V.b[r] - sell_dot<16, float>(V.sptr, V.col, V.val, V.x, r);
     }
     if (!team_sync(t)) return false;
     const float* rp = V.rpre;
@@ -736,7 +807,7 @@ __device__ __noinline__ bool ph_amg_up(Ctx& C, int l, double& rz, double& rr) {
         acc[1] += v.x * v.x;
     };
     if (l == 0) {
-        level0_products(P, t, V.u_sptr, V.u_col, V.u_val, yc, V.n, false, pre, row);
+        level0_products(P, t, V.u_sptr, V.u_col, V.u_val, nullptr, yc, V.n, false, pre, row);
     } else {
         ROWS(r, V.n) {
             const float2 v = pre(r);
@@ -815,7 +886,7 @@ __device__ bool ph_p32_direction(Ctx& C, float beta, double& dq) {
         P.pq32[p] = qn;
         acc[0] += v.x * qn;
     };
-    level0_products(P, t, P.p_sptr, P.p_col, P.Kp32, z, P.nphi, true, pre, row);
+    level0_products(P, t, P.k_sptr, P.k_col, P.Kp32, P.k_tab, z, P.nphi, true, pre, row);
     if (!team_sum_f32<1>(t, acc, out)) return false;
     dq = out[0];
     return true;

@@ -39,3 +39,17 @@ def test_step_bytes(bench):
     mg = bench.alg_bytes(st, sz, LEVELS) - base
     vc = bench.vcycle_bytes(LEVELS)
     assert mg == 18 * (8 * 15000 + 52 * 1000 + vc) + 2 * (12 * 15000 + 60 * 1000 + vc)
+
+
+def test_step_bytes_with_the_fp32_layout(bench):
+    """With the FP32 K_phi's own matrix bytes given (k32_bytes), the FP32
+    products (the direction pass and the level-0 down phase) count those
+    instead of 8 nnz_phi; the FP64 products keep 12 nnz_phi."""
+    kb = 70000
+    sz = {"n_phi": 1000, "n_mag": 100, "nnz_phi": 15000, "nnz_mag": 1400, "k32_bytes": kb}
+    st = {"mi": 20, "mr": 2, "evals": 3, "li": 4, "nli": 1}
+    base = bench.alg_bytes(dict(st, mi=0, mr=0), sz)
+    assert bench.alg_bytes(st, sz) - base == 18 * (kb + 52 * 1000) + 2 * (12 * 15000 + 60 * 1000)
+    vc = bench.vcycle_bytes(LEVELS, kb)
+    assert vc == bench.vcycle_bytes(LEVELS) - 8 * 15000 + kb
+    assert bench.alg_bytes(st, sz, LEVELS) - base == 18 * (kb + 52 * 1000 + vc) + 2 * (12 * 15000 + 60 * 1000 + vc)

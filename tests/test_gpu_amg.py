@@ -168,3 +168,38 @@ def test_tile_shapes_match_oracle(lib):
         assert np.abs(m - r.m).max() < 1e-5, key
         assert st["F"] == pytest.approx(s0["F"], rel=1e-10), key
         assert np.abs(m - m0).max() < 1e-6, key
+
+
+def test_table_layout_minimize_matches_oracle(lib):
+    """On an unjittered graded lattice most slices of the FP32 K_phi get an
+    offset table (values only; the slices that mix magnet-surface rows, whose
+    air neighbours are numbered after all magnetic nodes, keep columns: 267
+    of 489 slices have tables here); the precision forms that stream it
+    (Jacobi and multigrid) reach the oracle's minimum (energy 1e-8, max nodal
+    |dm| 1e-5).  A jittered mesh keeps its columns everywhere."""
+    Magnet, Params, _ = lib
+    jit = Magnet(device=0).upload_workload(_cube())
+    lay = jit.k32_layout()
+    assert lay["table_slices"] == 0 and lay["matrix_bytes"] >= 8 * jit.sizes()["nnz_phi"]
+    jit.close()
+    wl = synth.large_polycrystal(n_mag=14, edge=30e-9, n_grains=4)
+    P = fem.assemble_workload(wl)
+    b = wl.fields[3]
+    r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), P.units.field_int(b),
+                     ncg.Params(jmax=4, poisson="cg", poisson_tol=1e-12))
+    assert r.status == "converged"
+    for amg in (0, 1):
+        mag = Magnet(device=0)
+        mag.upload_workload(wl)
+        lay = mag.k32_layout()
+        assert lay["table_slices"] > 0.4 * lay["slices"]
+        assert lay["matrix_bytes"] < 0.9 * 8 * mag.sizes()["nnz_phi"]
+        assert amg == 0 or mag.amg_levels()
+        mag.set_magnetization(wl.m0)
+        mag.set_field(b)
+        st = mag.minimize(Params(jmax=4, precision=1, amg=amg, inner_tol=1e-3, poisson_tol=1e-12))
+        m = mag.get_magnetization()[P.mag_nodes]
+        assert st["status"] == "ok"
+        assert st["F"] == pytest.approx(r.F * P.units.energy_J, rel=1e-8)
+        assert np.abs(m - r.m).max() < 1e-5
+        mag.close()
