@@ -128,7 +128,7 @@ def vcycle_bytes(amg, k32_bytes=None):
     return tot
 
 
-def alg_bytes(st, sz, amg=None):
+def alg_bytes(st, sz, amg=None, precision=0):
     """Bytes one minimisation launch must move at ideal reuse (every array
     element read or written once per phase, neighbour gathers served from
     cache), from the launch's own counters:
@@ -144,8 +144,11 @@ def alg_bytes(st, sz, amg=None):
       evaluation (evals)    12 nnz_phi + 64 nnz_mag + 48 n_phi + 208 n_mag
                             (potential set-up incl. D m; energy/gradient pass)
       trial point (evals-1) 112 n_mag
-      inner step (li)       12 nnz_mag + 352 n_mag  (H product + update)
-      per iteration (nli+1) 272 n_mag               (inner set-up + direction)
+      inner step (li)       12 nnz_mag + 352 n_mag  (H product + update);
+                            precision form: 8 nnz_mag + 228 n_mag (FP32
+                            K_A and vectors; m, lambda, y in FP64)
+      per iteration (nli+1) 272 n_mag               (inner set-up + direction;
+                                                     precision form 244 n_mag)
     nnz_phi is the stored potential stiffness (without the rounding residues
     the upload drops).  The FP32 products' 8 nnz_phi (val+col) become
     sz["k32_bytes"] when given: the matrix bytes of the FP32 K_phi's own
@@ -160,8 +163,8 @@ def alg_bytes(st, sz, amg=None):
     per_refine = 12 * nzp + 60 * nphi        # FP64 residual product + FP32 set-up
     per_eval = 12 * nzp + 64 * nzm + 48 * nphi + 208 * nm
     per_trial = 112 * nm
-    per_inner = 12 * nzm + 352 * nm
-    per_iter = 272 * nm
+    per_inner = (8 * nzm + 228 * nm) if precision else (12 * nzm + 352 * nm)
+    per_iter = (244 if precision else 272) * nm
     mr = st.get("mr", 0)
     if amg:
         vc = vcycle_bytes(amg, kb)
@@ -495,7 +498,7 @@ def main():
             mag.minimize_async(prm)
             st = mag.get_stats()
             ms = mag.last_kernel_ms()
-            b = alg_bytes(st, sz, lv)
+            b = alg_bytes(st, sz, lv, prm.precision)
             kern_ms += ms
             nbytes += b
             nli += st["nli"]
@@ -886,7 +889,7 @@ def scaling_mode(args, rank, local_rank):
             mag.minimize_async(prm)
             st = mag.get_stats()
             kms += mag.last_kernel_ms()
-            nbytes += alg_bytes(st, sz, lv)
+            nbytes += alg_bytes(st, sz, lv, prm.precision)
             nli += st["nli"]
             mi += st["mi"]
             ev += st["evals"]

@@ -90,7 +90,11 @@ typedef struct {
                            /* potential solve runs Algorithm 1 in FP32 on the      */
                            /* correction equation K delta = r and refines the      */
                            /* residual r = D m - K phi in FP64 ("reliable          */
-                           /* updates") until poisson_tol                          */
+                           /* updates") until poisson_tol; the preconditioner     */
+                           /* apply (Eq. precond) forms its H products and inner  */
+                           /* CG vectors in FP32 (sums, step lengths and y FP64); */
+                           /* energy, gradient, line search, beta and the         */
+                           /* renormalisation stay FP64                            */
     double inner_tol;      /* FP32 residual drop that triggers an FP64 update (0.1)*/
     int max_refine;        /* cap on FP64 updates per potential solve (64)         */
     int amg;               /* precision form: 1 = precondition the FP32 solve with */
@@ -268,7 +272,8 @@ int mm_get_potential(mm_ctx* ctx, double* phi_out);
 /* Truncated preconditioner solve of Eq. (precond) by Algorithm 1 with
  * li1-li3 (Sec. 2.2, 3.1) at the state of the last evaluation (mm_energy or
  * mm_gradient): y ~ H(m)^{-1} g for the projected gradient g there.
- * y_out [n_nodes][3]; *steps (may be NULL) = products with H. */
+ * y_out [n_nodes][3]; *steps (may be NULL) = products with H.  With
+ * p->precision = 1, the precision form's FP32 apply. */
 int mm_precond_solve(mm_ctx* ctx, const mm_params* p, double* y_out,
                      int64_t* steps);
 

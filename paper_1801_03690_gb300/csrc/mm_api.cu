@@ -1401,6 +1401,24 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     if ((rc = dalloc(ctx, &P.idir[0], v3))) return rc;
     if ((rc = dalloc(ctx, &P.idir[1], v3))) return rc;
     if ((rc = dalloc(ctx, &P.ihd, v3))) return rc;
+    {
+        // FP32 copies for the precision form's preconditioner apply
+        float *ka32, *ck32, *da32;
+        if ((rc = dalloc(ctx, &ka32, nnzm))) return rc;
+        if ((rc = dalloc(ctx, &ck32, 6 * (size_t)nm))) return rc;
+        if ((rc = dalloc(ctx, &da32, nm))) return rc;
+        k_to_f32<<<nblk(nnzm), 256, 0, ctx->stream>>>(nnzm, KA, ka32);
+        k_to_f32<<<nblk(6 * (long long)nm), 256, 0, ctx->stream>>>(6 * (long long)nm, CK, ck32);
+        k_to_f32<<<nblk(nm), 256, 0, ctx->stream>>>(nm, dinvA, da32);
+        CK_CUDA(cudaGetLastError());
+        P.KA32 = ka32;
+        P.CK32 = ck32;
+        P.dinvA32 = da32;
+        if ((rc = dalloc(ctx, &P.ires32, v3))) return rc;
+        if ((rc = dalloc(ctx, &P.iprec32, v3))) return rc;
+        if ((rc = dalloc(ctx, &P.idir32, v3))) return rc;
+        if ((rc = dalloc(ctx, &P.ihd32, v3))) return rc;
+    }
     if ((rc = dalloc(ctx, &P.phi, nphi))) return rc;
     for (int s = 0; s < MM_NSLOT; ++s)
         if ((rc = dalloc(ctx, &P.PHI[s], nphi))) return rc;
@@ -1465,6 +1483,8 @@ int mm_upload_mesh(mm_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_te
     CK_CUDA(z(P.idir[0], v3));
     CK_CUDA(z(P.idir[1], v3));
     CK_CUDA(z(P.ihd, v3));
+    for (float* f : {P.ires32, P.iprec32, P.idir32, P.ihd32})
+        CK_CUDA(cudaMemsetAsync(f, 0, v3 * sizeof(float), ctx->stream));
     CK_CUDA(z(P.phi, nphi));
     for (int s = 0; s < MM_NSLOT; ++s) CK_CUDA(z(P.PHI[s], nphi));
     CK_CUDA(z(P.rhs, nm));

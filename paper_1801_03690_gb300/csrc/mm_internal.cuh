@@ -145,6 +145,15 @@ struct Problem {
     double* iprec;           // [3][nm] Jacobi-preconditioned residual
     double* idir[2];         // [3][nm] direction (double buffer)
     double* ihd;             // [3][nm] H * direction
+    // precision form: the inner solve's H products and vectors in FP32
+    // (isol stays FP64: the search direction is built from it)
+    const float* KA32;       // [nnzm] K_A on the magnetic graph's SELL-32
+    const float* CK32;       // [6][nm]
+    const float* dinvA32;    // [nm]
+    float* ires32;           // [3][nm]
+    float* iprec32;          // [3][nm]
+    float* idir32;           // [3][nm]
+    float* ihd32;            // [3][nm]
     // potential solve (Algorithm 1 on K_phi)
     double* phi;             // [nphi] working potential (the last solve)
     double* PHI[MM_NSLOT];   // [nphi] potential of each state slot

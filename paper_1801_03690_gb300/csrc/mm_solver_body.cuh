@@ -254,22 +254,24 @@ __device__ __forceinline__ T sell_dot(const long long* __restrict__ sptr, const 
     return sell_dot<CH, T>(sptr, col, val, x, r, r);
 }
 
-// Same for a scalar matrix applied to a SoA 3-vector (stride n).
-template <int CH>
+// Same for a scalar matrix applied to a SoA 3-vector (stride n); T the
+// type of the sums and of the values (FP64, or FP32 in the precision form's
+// preconditioner).
+template <int CH, typename T>
 __device__ __forceinline__ void sell_dot3(const long long* __restrict__ sptr, const int* __restrict__ col,
-                                          const double* __restrict__ val, const double* x, int n, int r,
-                                          double& s0, double& s1, double& s2) {
+                                          const T* __restrict__ val, const T* x, int n, int r,
+                                          T& s0, T& s1, T& s2) {
     const Row A = sell_row(sptr, r);
-    s0 = s1 = s2 = 0.0;
+    s0 = s1 = s2 = T(0);
     for (int k0 = 0; k0 < A.width; k0 += CH) {
         int c[CH];
-        double v[CH];
+        T v[CH];
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             const bool ok = k0 + u < A.width;
             const long long e = A.base + 32ll * (k0 + u);
             c[u] = ok ? __ldg(col + e) : r;
-            v[u] = ok ? __ldg(val + e) : 0.0;
+            v[u] = ok ? __ldg(val + e) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
@@ -1312,6 +1314,138 @@ __device__ bool precond_solve(Ctx& C, int s) {
     return true;                                // li1
 }
 
+// The precision form's preconditioner apply: precond_solve with H's
+// products and the residual, preconditioned-residual, direction and
+// H-direction vectors in FP32 (K_A, C_K and diag(C_A)^-1 as FP32 copies);
+// m, lambda and the gradient are read from the FP64 state, the dots are
+// FP32 products summed in FP64, the step length and beta stay FP64 scalars
+// and the solution y accumulates in FP64 (the search direction is built from
+// it).  The exits li1-li3 and their counters are those of precond_solve.
+__device__ bool ph_hess32(Ctx& C, int s, const float* v, float beta, float* d, float* hd, double& dHd) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const double* m = P.X[s];
+    const double* lamv = P.LAM[s];
+    const double* gr = P.GR[s];
+    const bool keep = P.prm.keep_last_term != 0;
+    const bool first = (beta == 0.0f);
+    double acc[1] = {0.0};
+    double dummy[1] = {0.0};
+    ROWS(i, nm) {
+        float c0, c1, c2;
+        sell_dot3<8>(P.m_sptr, P.m_col, P.KA32, v, nm, i, c0, c1, c2);
+        const float v0 = v[i], v1 = v[nm + i], v2 = v[2 * nm + i];
+        const float kxx = P.CK32[i], kxy = P.CK32[nm + i], kxz = P.CK32[2 * nm + i];
+        const float kyy = P.CK32[3 * nm + i], kyz = P.CK32[4 * nm + i], kzz = P.CK32[5 * nm + i];
+        const float Cv0 = 2.0f * c0 + (kxx * v0 + kxy * v1 + kxz * v2);
+        const float Cv1 = 2.0f * c1 + (kxy * v0 + kyy * v1 + kyz * v2);
+        const float Cv2 = 2.0f * c2 + (kxz * v0 + kyz * v1 + kzz * v2);
+        const float m0 = (float)m[i], m1 = (float)m[nm + i], m2 = (float)m[2 * nm + i];
+        const float mc = m0 * Cv0 + m1 * Cv1 + m2 * Cv2;
+        const float lam = (float)lamv[i];
+        float w[3] = {Cv0 - mc * m0 - lam * v0, Cv1 - mc * m1 - lam * v1, Cv2 - mc * m2 - lam * v2};
+        if (keep) {
+            const float vg = v0 * (float)gr[i] + v1 * (float)gr[nm + i] + v2 * (float)gr[2 * nm + i];
+            w[0] -= vg * m0;
+            w[1] -= vg * m1;
+            w[2] -= vg * m2;
+        }
+        const float vv[3] = {v0, v1, v2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            // d = -v + beta d, hd = -H v + beta hd (= H d)
+            float dn = -vv[c], hn = -w[c];
+            if (!first) {
+                dn += beta * d[c * nm + i];
+                hn += beta * hd[c * nm + i];
+            }
+            d[c * nm + i] = dn;
+            hd[c * nm + i] = hn;
+            acc[0] += (double)(dn * hn);
+        }
+    }
+    if (!team_reduce<1, 0>(t, acc, dummy)) return false;
+    dHd = acc[0];
+    return true;
+}
+
+__device__ bool precond_solve32(Ctx& C, int s) {
+    const Problem& P = *C.P;
+    Team& t = C.t;
+    const int nm = P.nm;
+    const int jmax = P.prm.jmax;
+    if (jmax <= 0) {
+        C.y_is_g = 1;
+        return true;
+    }
+    const double* g = P.GP[s];
+    double acc[2] = {0.0, 0.0};
+    double dummy[1] = {0.0};
+    ROWS(i, nm) {
+        const float di = P.dinvA32[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float r = (float)(-g[c * nm + i]);
+            const float z = di * r;
+            P.ires32[c * nm + i] = r;
+            P.iprec32[c * nm + i] = z;
+            P.isol[c * nm + i] = 0.0;
+            acc[0] += (double)(r * z);
+            acc[1] += (double)(r * r);
+        }
+    }
+    if (!team_reduce<2, 0>(t, acc, dummy)) return false;
+    double gy = acc[0];
+    const double ng = sqrt(acc[1]);
+    const double eps = fmin(0.5, sqrt(ng)) * ng;
+    C.y_is_g = 0;
+    if (ng < eps) return true;
+    double beta = 0.0;
+    int steps = 0;
+    while (steps < jmax) {
+        double dHd;
+        if (!ph_hess32(C, s, P.iprec32, (float)beta, P.idir32, P.ihd32, dHd)) return false;
+        ++steps;
+        C.li++;
+        if (dHd <= 0.0) {                       // li2
+            C.li2++;
+            if (steps == 1) {
+                C.y_is_g = 1;
+                C.li2_first++;
+            }
+            return true;
+        }
+        const double a = gy / dHd;
+        const float af = (float)a;
+        double a2[2] = {0.0, 0.0};
+        ROWS(i, nm) {
+            const float di = P.dinvA32[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int q = c * nm + i;
+                P.isol[q] += a * (double)P.idir32[q];
+                const float r = P.ires32[q] + af * P.ihd32[q];
+                const float z = di * r;
+                P.ires32[q] = r;
+                P.iprec32[q] = z;
+                a2[0] += (double)(r * z);
+                a2[1] += (double)(r * r);
+            }
+        }
+        if (!team_reduce<2, 0>(t, a2, dummy)) return false;
+        if (sqrt(a2[1]) < eps) return true;     // li3
+        beta = a2[0] / gy;
+        gy = a2[0];
+    }
+    return true;                                // li1
+}
+
+// The preconditioner apply of the configured form.
+__device__ bool precond_apply(Ctx& C, int s) {
+    return C.P->prm.precision ? precond_solve32(C, s) : precond_solve(C, s);
+}
+
 // beta*ZA dots between slot a (new gradient gn) and slot c (old gradient go)
 // with y the preconditioned gn and d the previous direction:
 //   y.gn, y.go, (gn-go).y, (gn-go).d, gn.d, gn.gn, gn.go, (gn-go).gn
@@ -1439,7 +1573,7 @@ __device__ int minimize(Ctx& C, int& cur) {
     const Params& prm = P.prm;
     int c = cur;
     if (!evaluate(C, c, c, false, 0.0)) return ST_TIMEOUT;
-    if (!precond_solve(C, c)) return ST_TIMEOUT;
+    if (!precond_apply(C, c)) return ST_TIMEOUT;
     double dmax, gd;
     if (!direction(C, c, c, true, dmax, gd)) return ST_TIMEOUT;
     double a_prev = 1.0;
@@ -1508,7 +1642,7 @@ __device__ int minimize(Ctx& C, int& cur) {
         const bool t1 = F0 - S.F < prm.tau_F * (1.0 + fabs(S.F));
         const bool t2 = S.xdiff < sq_tau * (1.0 + S.xmax);
         const bool t3 = S.gmax < cb_tau * (1.0 + fabs(S.F));
-        if (!precond_solve(C, b)) return ST_TIMEOUT;
+        if (!precond_apply(C, b)) return ST_TIMEOUT;
         if (!direction(C, b, c, false, dmax, gd)) return ST_TIMEOUT;
         c = b;
         a_prev = a_b;
@@ -1553,7 +1687,7 @@ __device__ __forceinline__ void solver_body(const Problem& P, int nb, int rank) 
             if (!evaluate(C, cur, cur, false, 0.0)) status = ST_TIMEOUT;
             break;
         case MODE_PRECOND:
-            if (!precond_solve(C, cur)) status = ST_TIMEOUT;
+            if (!precond_apply(C, cur)) status = ST_TIMEOUT;
             break;
         case MODE_HESS: {
             // input v in idir[0], output in ihd

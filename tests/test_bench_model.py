@@ -53,3 +53,17 @@ def test_step_bytes_with_the_fp32_layout(bench):
     vc = bench.vcycle_bytes(LEVELS, kb)
     assert vc == bench.vcycle_bytes(LEVELS) - 8 * 15000 + kb
     assert bench.alg_bytes(st, sz, LEVELS) - base == 18 * (kb + 52 * 1000 + vc) + 2 * (12 * 15000 + 60 * 1000 + vc)
+
+
+def test_inner_step_bytes_of_the_precision_form(bench):
+    """The precision form's preconditioner runs in FP32: an inner step moves
+    8 nnz_mag + 228 n_mag, the per-iteration set-up and direction 244 n_mag,
+    against 12 nnz_mag + 352 n_mag and 272 n_mag in FP64."""
+    sz = {"n_phi": 1000, "n_mag": 100, "nnz_phi": 15000, "nnz_mag": 1400}
+    st = {"mi": 0, "mr": 0, "evals": 3, "li": 4, "nli": 1}
+    d64 = bench.alg_bytes(st, sz) - bench.alg_bytes(dict(st, li=0), sz)
+    d32 = bench.alg_bytes(st, sz, precision=1) - bench.alg_bytes(dict(st, li=0), sz, precision=1)
+    assert d64 == 4 * (12 * 1400 + 352 * 100) and d32 == 4 * (8 * 1400 + 228 * 100)
+    i64 = bench.alg_bytes(st, sz) - bench.alg_bytes(dict(st, nli=0), sz)
+    i32 = bench.alg_bytes(st, sz, precision=1) - bench.alg_bytes(dict(st, nli=0), sz, precision=1)
+    assert i64 == 272 * 100 and i32 == 244 * 100

@@ -145,6 +145,28 @@ def test_precond_solve(lib, jmax):
     np.testing.assert_allclose(y[P.mag_nodes], y_or, rtol=0, atol=1e-10 * np.abs(y_or).max())
 
 
+@pytest.mark.parametrize("jmax", [1, 4, 12])
+def test_precond_solve_fp32(lib, jmax):
+    """The precision form's preconditioner apply (H products and the inner
+    CG's vectors in FP32; sums, step lengths and the solution in FP64)
+    against the oracle's FP64 Algorithm 1 on H: the same number of steps
+    (one more or less where an li3 test sits at the FP32 rounding level) and
+    y within 1e-3 of its largest entry."""
+    Magnet, Params = lib
+    wl = _hard()
+    mag, P = _setup(lib, wl)
+    mag.set_field([0.0, 0.0, 2.0])
+    grad = mag.gradient(wl.m0, projected=False, params=Params(**TIGHT))[P.mag_nodes]
+    mo = energy.normalize(wl.m0[P.mag_nodes])
+    g = energy.project(mo, grad)
+    y, steps = mag.precond_solve(Params(jmax=jmax, precision=1))
+    y_or, steps_or = precond.precond_solve(P, mo, grad, g, jmax)
+    dev = np.abs(y[P.mag_nodes] - y_or).max() / np.abs(y_or).max()
+    print(f"FP32 preconditioner, j_max {jmax}: steps {steps} (oracle {steps_or}), deviation {dev:.2e}")
+    assert abs(steps - steps_or) <= 1
+    assert dev < 1e-3
+
+
 @pytest.mark.parametrize("jmax", [0, 4])
 def test_minimize_parity_soft(lib, jmax):
     Magnet, Params = lib
