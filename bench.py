@@ -264,6 +264,75 @@ def traffic_record(workload_name):
     return None
 
 
+def _ncu_launches(csv_path):
+    """Per-launch metrics of an ncu --csv --print-units base log: a list of
+    {"id", "kernel", metric: value} in launch order."""
+    import csv
+    rows = {}
+    with open(csv_path, newline="") as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        lid = int(r["ID"])
+        d = rows.setdefault(lid, {"id": lid, "kernel": r["Kernel Name"]})
+        try:
+            d[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+        except ValueError:
+            pass
+    return [rows[k] for k in sorted(rows)]
+
+
+def record_traffic(csv_path, line_path, command):
+    """Writes profiles/k_solver_traffic.json from one ncu capture of the
+    profiling command (`--workload polycrystal_medium --steps 1 --warmup 1
+    --fp64-steps 1 --no-curve --no-cpu-baseline --no-e2e`) with
+    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum
+    on every launch, and that run's own JSON line.  The solver launches of
+    that command are, in order: warm-up (headline form, field 0), the
+    untimed re-convergence of field 0 and the timed field 1 in the headline
+    form, then the same two in plain FP64; the ratio DRAM bytes /
+    algorithmic bytes of the timed launches is recorded for the captured
+    workload and, scaled by the launch's algorithmic bytes, for the large
+    polycrystal (same recipe and kernel; traffic grows with the bytes the
+    counters imply)."""
+    ls = [d for d in _ncu_launches(csv_path) if "k_solver" in d["kernel"]]
+    if len(ls) != 5:
+        raise SystemExit(f"expected 5 solver launches in {csv_path}, found {len(ls)}")
+    line = None
+    for ln in open(line_path):
+        if ln.startswith("{"):
+            line = json.loads(ln)
+    if line is None:
+        raise SystemExit(f"no JSON line in {line_path}")
+    out = {"kernel_sources": KERNEL_SOURCES, "records": []}
+    forms = (("headline", ls[2], line["timed_fields"]["per_step"][0]),
+             ("plain_fp64", ls[4], line["plain_fp64"]["per_step"][0]))
+    for form, d, st in forms:
+        tr = d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"]
+        alg = st["alg_GB"] * 1e9
+        ratio = tr / alg
+        base = {"form": form, "sources": kernel_source_digest(), "ratio": ratio,
+                "captured_on": "polycrystal_medium", "dram_bytes_read": d["dram__bytes_read.sum"],
+                "dram_bytes_write": d["dram__bytes_write.sum"], "alg_bytes": alg,
+                "gpu_time_ns": d.get("gpu__time_duration.sum"), "kernel": d["kernel"],
+                "counters": {k: st[k] for k in ("nli", "evals", "mi", "mr", "li")},
+                "command": command}
+        if form == "headline":
+            out["records"].append(dict(base, workload="polycrystal_medium",
+                                       note="measured on this workload's timed launch"))
+            out["records"].append(dict(base, workload="large_polycrystal",
+                                       note="ratio from the 3.2 M-unknown medium case of the same recipe, "
+                                            "scaled to the full launch by its algorithmic bytes"))
+        else:
+            out["records"].append(dict(base, workload="polycrystal_medium/plain_fp64",
+                                       note="plain FP64 form, measured on this workload's timed launch"))
+    with open(os.path.join(ROOT, TRAFFIC), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    for r in out["records"]:
+        print(f"{r['workload']}: traffic {r['dram_bytes_read'] + r['dram_bytes_write']:.4g} B, "
+              f"algorithmic {r['alg_bytes']:.4g} B, ratio {r['ratio']:.3f}")
+
+
 # ------------------------------------------------------------------ ranks
 class Ranks:
     """Replicas only: every rank solves its own copy of the workload; the
@@ -298,7 +367,7 @@ class Ranks:
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(name, first_field, n_iter):
+def oracle_sample(name, first_field, n_iter, sample=True):
     """The CPU oracle as it stands, on the reduced-resolution sample of the
     workload's recipe (workload(name, sample=True)): assembly, then
     Algorithm 4 with the potential solved by Algorithm 1 (the same algorithm
@@ -307,7 +376,7 @@ def oracle_sample(name, first_field, n_iter):
     whenever a field converges first.  Returns a dict with the timed
     seconds (assembly excluded), the counters and the sample's sizes."""
     from oracle import fem, energy, ncg
-    wl = workload(name, sample=True)
+    wl = workload(name, sample=sample)
     t0 = time.perf_counter()
     P = fem.assemble_workload(wl)
     t_asm = time.perf_counter() - t0
@@ -367,6 +436,77 @@ def oracle_baseline_entry(o, full=None):
     return e
 
 
+# ------------------------------------------------------------------ oracle plan
+def oracle_plan_leg(kind, name):
+    """One leg of the CPU-baseline plan, run in this process (the caller
+    sets its thread count): 'curve' = the oracle's whole demagnetisation
+    curve of the workload (Sec. 3.1 field loop, Algorithm 4 per field);
+    'iters' = 5 NCG iterations at full size from field index 5 (the first
+    field the GPU bench times), continuing into the next fields;
+    'sample' = the same on the workload's reduced-resolution sample;
+    'platelets' = 5 iterations from m0 at the first field on each of the
+    first 4 platelets of the seeded batch."""
+    from oracle import fem, curve, ncg, energy
+    prm = ncg.Params(jmax=4, poisson="cg")
+    if kind == "curve":
+        wl = workload(name)
+        t0 = time.perf_counter()
+        P = fem.assemble_workload(wl)
+        t_asm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r = curve.demag_curve(P, wl.fields, wl.m0, prm)
+        dt = time.perf_counter() - t0
+        recs = r["records"]
+        return {"kind": kind, "workload": wl.name, "seconds": dt, "assembly_s": t_asm,
+                "fields": len(recs), "nli": int(sum(x["nli"] for x in recs)),
+                "evals": int(sum(x["evals"] for x in recs)), "mi": int(sum(x["mi"] for x in recs)),
+                "Hc_T": r["Hc_T"], "n_phi": P.n_phi, "n_mag": P.n_mag}
+    if kind in ("iters", "sample"):
+        o = oracle_sample(name, 5, 5, sample=(kind == "sample"))
+        return dict(o, kind=kind, workload=o["sample"])
+    if kind == "platelets":
+        import synth
+        out = []
+        for wl in synth.platelet_batch(64)[:4]:
+            P = fem.assemble_workload(wl)
+            m = energy.normalize(wl.m0[P.mag_nodes])
+            t0 = time.perf_counter()
+            r = ncg.minimize(P, m, P.units.field_int(wl.fields[0]), ncg.Params(jmax=4, poisson="cg", max_iter=5))
+            out.append({"platelet": wl.name, "n_mag": P.n_mag, "n_phi": P.n_phi, "nli": r.stats["nli"],
+                        "seconds": time.perf_counter() - t0})
+        return {"kind": kind, "platelets": out}
+    raise ValueError(kind)
+
+
+def oracle_plan_mode(args):
+    """The CPU-baseline plan: every leg once single-threaded and once with
+    the BLAS / OpenMP pools at the core count, in child processes.  CPU
+    only; prints one JSON object per leg and a summary line."""
+    legs = [("curve", "soft_cube"), ("iters", "hard_cube"), ("sample", "polycrystal"),
+            ("sample", "large_polycrystal"), ("platelets", "platelets")]
+    if args.plan_legs:
+        want = set(args.plan_legs.split(","))
+        legs = [l for l in legs if f"{l[0]}:{l[1]}" in want]
+    cores = os.cpu_count() or 1
+    res = []
+    for kind, name in legs:
+        for threads in sorted({1, cores}):
+            env = dict(os.environ)
+            for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+                env[v] = str(threads)
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-plan-leg", kind, name],
+                               capture_output=True, text=True, env=env, cwd=ROOT)
+            if r.returncode != 0:
+                raise RuntimeError("oracle plan leg failed:\n" + r.stderr[-2000:])
+            o = json.loads(r.stdout.strip().splitlines()[-1])
+            o["threads"] = threads
+            print(json.dumps(o), flush=True)
+            res.append(o)
+    import platform
+    print(json.dumps({"mode": "oracle_plan", "host": platform.machine(), "cores": cores, "legs": len(res)}))
+    return 0
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -383,11 +523,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-curve", action="store_true", help="skip the full hard-cube curves")
-    ap.add_argument("--mode", default="steps", choices=["steps", "curve", "batch", "scaling", "sp3", "mlp"],
+    ap.add_argument("--mode", default="steps",
+                    choices=["steps", "curve", "batch", "scaling", "sp3", "mlp", "oracle_plan"],
                     help="steps: the timed field steps (default line); curve: full demagnetisation "
                          "curves of the plain FP64, precision and precision + learned forms; "
                          "batch: the batched platelet workload; scaling: field steps of the hard "
-                         "cube at several resolutions")
+                         "cube at several resolutions; oracle_plan: the CPU oracle's timing plan "
+                         "(CPU only)")
     ap.add_argument("--n-platelets", type=int, default=64)
     ap.add_argument("--sp3-edges", default="8.2,8.4,8.6,8.8", help="sp3 mode: cube edges in exchange lengths")
     ap.add_argument("--sp3-n", type=int, default=24, help="sp3 mode: voxels per cube edge")
@@ -404,9 +546,22 @@ def main():
     ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-first-field", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-iters", type=int, default=5, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-plan-leg", nargs=2, metavar=("KIND", "WORKLOAD"), help=argparse.SUPPRESS)
+    ap.add_argument("--plan-legs", default="", help="oracle_plan mode: kind:workload legs to run (default all)")
+    ap.add_argument("--record-traffic", nargs=3, metavar=("NCU_CSV", "JSON_LINE", "COMMAND"),
+                    help="write profiles/k_solver_traffic.json from an ncu capture of the profiling command "
+                         "(no GPU needed)")
     args = ap.parse_args()
     K, W = args.steps, max(args.warmup, 0)
 
+    if args.record_traffic:
+        record_traffic(*args.record_traffic)
+        return 0
+    if args.oracle_plan_leg:
+        print(json.dumps(oracle_plan_leg(*args.oracle_plan_leg)))
+        return 0
+    if args.mode == "oracle_plan":
+        return oracle_plan_mode(args)
     if args.oracle_leg:
         print(json.dumps(oracle_sample(args.workload, args.oracle_first_field, args.oracle_iters)))
         return 0
