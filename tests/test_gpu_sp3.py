@@ -7,8 +7,10 @@ paper finds at 8.52 l_ex (Hertel and Kronmueller: 8.56 l_ex).  The mesh is
 h ~ 0.35 l_ex (24 voxels per edge) in a graded air box of 8 times the edge
 (measured: 8.51 l_ex; a box of 4 edges lowers the flower state's
 stray-field energy enough to move the crossover to 8.64 l_ex); the
-crossover is required within 1.5% of 8.52 l_ex.  On the smallest edge at
-16 voxels both states are checked against the oracle.""" 
+crossover is required within 1.5% of 8.52 l_ex.  On the smallest edge both
+states are checked against the oracle on the same mesh at 12 voxels per
+edge (the parity check needs the same mesh on both sides, not the fine one;
+the oracle's vortex relaxation takes about 2 minutes there, 6 at 16).""" 
 import numpy as np
 import pytest
 
@@ -60,7 +62,7 @@ def test_states_match_oracle_on_the_smallest_edge():
     energy within 1e-4 relative and the same closure |M| within 0.02."""
     L = EDGES[0]
     for start in ("flower", "vortex"):
-        wl, st, m, e = _relax(L, start, 16)
+        wl, st, m, e = _relax(L, start, 12)
         P = fem.assemble_workload(wl)
         r = ncg.minimize(P, energy.normalize(wl.m0[P.mag_nodes]), np.zeros(3),
                          ncg.Params(tau_F=1e-12, jmax=12, max_iter=100000))
