@@ -281,7 +281,7 @@ def _ncu_launches(csv_path):
     return [rows[k] for k in sorted(rows)]
 
 
-def record_traffic(csv_path, line_path, command):
+def record_traffic(csv_path, line_path, command, out_path=None):
     """Writes profiles/k_solver_traffic.json from one ncu capture of the
     profiling command (`--workload polycrystal_medium --steps 1 --warmup 1
     --fp64-steps 1 --no-curve --no-cpu-baseline --no-e2e`) with
@@ -325,7 +325,7 @@ def record_traffic(csv_path, line_path, command):
         else:
             out["records"].append(dict(base, workload="polycrystal_medium/plain_fp64",
                                        note="plain FP64 form, measured on this workload's timed launch"))
-    with open(os.path.join(ROOT, TRAFFIC), "w") as f:
+    with open(out_path or os.path.join(ROOT, TRAFFIC), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
     for r in out["records"]:

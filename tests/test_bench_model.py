@@ -2,6 +2,7 @@
 the multigrid V-cycle bytes against the per-level formula written out, and
 the precision forms' step bytes against their definitions."""
 import importlib.util
+import json
 import os
 
 import pytest
@@ -67,3 +68,52 @@ def test_inner_step_bytes_of_the_precision_form(bench):
     i64 = bench.alg_bytes(st, sz) - bench.alg_bytes(dict(st, nli=0), sz)
     i32 = bench.alg_bytes(st, sz, precision=1) - bench.alg_bytes(dict(st, nli=0), sz, precision=1)
     assert i64 == 272 * 100 and i32 == 244 * 100
+
+
+def _ncu_csv(path, launches):
+    """An ncu --csv --print-units base log: banner lines, then one row per
+    launch and metric."""
+    hdr = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
+           "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]
+    lines = ["==PROF== Connected to process 1", ",".join(f'"{h}"' for h in hdr)]
+    for i, (kern, rd, wr, ns) in enumerate(launches):
+        for name, unit, v in (("dram__bytes_read.sum", "byte", rd), ("dram__bytes_write.sum", "byte", wr),
+                              ("gpu__time_duration.sum", "nsecond", ns)):
+            row = [str(i), "1", "python3", "host", kern, "1", "7", "(256, 1, 1)", "(608, 1, 1)", "0", "10.3",
+                   "Command line profiler metrics", name, unit, f"{v:,}"]
+            lines.append(",".join(f'"{x}"' for x in row))
+    open(path, "w").write("\n".join(lines) + "\n")
+
+
+def test_traffic_record_from_an_ncu_log(bench, tmp_path):
+    """--record-traffic takes the third and fifth solver launches of the
+    profiling command (the timed headline and plain FP64 field steps),
+    divides their DRAM bytes by the algorithmic bytes of the run's own JSON
+    line, and the bench finds the record only under the current kernel
+    source digest."""
+    solver = "void mm::k_solver<4>(mm::Problem)"
+    _ncu_csv(tmp_path / "l.csv", [("mm::k_tet_geometry(long)", 10, 0, 5), (solver, 1, 1, 1), (solver, 2, 2, 2),
+                                  (solver, 300, 60, 900), ("k_set_field(x)", 0, 0, 1), (solver, 4, 4, 4),
+                                  (solver, 2000, 500, 7000)])
+    line = {"timed_fields": {"per_step": [{"alg_GB": 0.3, "nli": 8, "evals": 17, "mi": 270, "mr": 21, "li": 21}]},
+            "plain_fp64": {"per_step": [{"alg_GB": 2.0, "nli": 8, "evals": 17, "mi": 7000, "mr": 0, "li": 19}]}}
+    (tmp_path / "j.log").write_text("noise\n" + json.dumps(line) + "\n")
+    out = tmp_path / "t.json"
+    bench.record_traffic(str(tmp_path / "l.csv"), str(tmp_path / "j.log"), "cmd", out_path=str(out))
+    recs = {r["workload"]: r for r in json.load(open(out))["records"]}
+    assert recs["polycrystal_medium"]["ratio"] == pytest.approx(360 / 0.3e9)
+    assert recs["large_polycrystal"]["ratio"] == recs["polycrystal_medium"]["ratio"]
+    assert recs["polycrystal_medium/plain_fp64"]["ratio"] == pytest.approx(2500 / 2.0e9)
+    assert recs["polycrystal_medium"]["gpu_time_ns"] == 900
+    old = bench.TRAFFIC
+    try:
+        bench.TRAFFIC = str(out)                      # an absolute path: os.path.join keeps it
+        assert bench.traffic_record("large_polycrystal")["ratio"] == pytest.approx(360 / 0.3e9)
+        assert bench.traffic_record("hard_cube") is None
+        d = json.load(open(out))
+        for r in d["records"]:
+            r["sources"] = "0" * 16                   # as if the kernel sources had changed since
+        json.dump(d, open(out, "w"))
+        assert bench.traffic_record("large_polycrystal") is None
+    finally:
+        bench.TRAFFIC = old
