@@ -367,46 +367,59 @@ class Ranks:
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(name, first_field, n_iter, sample=True):
+def oracle_sample(name, first_field, n_iter, sample=True, warm_iter=0):
     """The CPU oracle as it stands, on the reduced-resolution sample of the
     workload's recipe (workload(name, sample=True)): assembly, then
     Algorithm 4 with the potential solved by Algorithm 1 (the same algorithm
-    as the GPU's plain FP64 form) from m0 at field index first_field, for
-    exactly n_iter NCG iterations, continuing into the next field indices
-    whenever a field converges first.  Returns a dict with the timed
-    seconds (assembly excluded), the counters and the sample's sizes."""
+    as the GPU's plain FP64 form) from m0 at field index first_field:
+    warm_iter untimed NCG iterations, then exactly n_iter timed ones,
+    continuing into the next field indices whenever a field converges (a
+    field left at the warm-up's iteration cap is resumed).  Returns a dict
+    with the timed seconds (assembly and warm-up excluded), the timed
+    counters and the sample's sizes."""
     from oracle import fem, energy, ncg
     wl = workload(name, sample=sample)
     t0 = time.perf_counter()
     P = fem.assemble_workload(wl)
     t_asm = time.perf_counter() - t0
-    m = energy.normalize(wl.m0[P.mag_nodes])
-    phi = None
+    state = {"m": energy.normalize(wl.m0[P.mag_nodes]), "phi": None, "k": first_field}
+
+    def run(budget, tot, fields):
+        while budget > 0 and state["k"] < len(wl.fields):
+            k = state["k"]
+            r = ncg.minimize(P, state["m"], P.units.field_int(wl.fields[k]),
+                             ncg.Params(jmax=4, poisson="cg", max_iter=budget), phi0=state["phi"])
+            state["m"], state["phi"] = r.m, r.phi
+            budget -= r.stats["nli"]
+            for c in tot:
+                tot[c] += r.stats[c]
+            if not fields or fields[-1] != k:
+                fields.append(k)
+            if r.status != "max_iter" or r.stats["nli"] == 0:
+                state["k"] = k + 1
+
+    t0 = time.perf_counter()
+    warm = {"nli": 0, "evals": 0, "mi": 0, "li": 0, "ls_extra": 0}
+    run(warm_iter, warm, [])
+    t_warm = time.perf_counter() - t0
     tot = {"nli": 0, "evals": 0, "mi": 0, "li": 0, "ls_extra": 0}
     fields = []
-    k = first_field
     t0 = time.perf_counter()
-    while tot["nli"] < n_iter and k < len(wl.fields):
-        r = ncg.minimize(P, m, P.units.field_int(wl.fields[k]),
-                         ncg.Params(jmax=4, poisson="cg", max_iter=n_iter - tot["nli"]), phi0=phi)
-        m, phi = r.m, r.phi
-        for c in tot:
-            tot[c] += r.stats[c]
-        fields.append(k)
-        k += 1
+    run(n_iter, tot, fields)
     dt = time.perf_counter() - t0
     return {"seconds": dt, "assembly_s": t_asm, **tot, "fields": fields, "sample": wl.name,
-            "n_phi": P.n_phi, "n_mag": P.n_mag}
+            "n_phi": P.n_phi, "n_mag": P.n_mag, "warm_iter": warm["nli"], "warm_s": t_warm}
 
 
-def oracle_leg(name, first_field, n_iter, threads):
+def oracle_leg(name, first_field, n_iter, threads, warm_iter=0):
     """oracle_sample in a child process whose BLAS / OpenMP pools have
     `threads` threads (numpy reads the setting at import)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[v] = str(threads)
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", "--workload", name,
-                        "--oracle-first-field", str(first_field), "--oracle-iters", str(n_iter)],
+                        "--oracle-first-field", str(first_field), "--oracle-iters", str(n_iter),
+                        "--oracle-warm-iters", str(warm_iter)],
                        capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle leg failed:\n" + r.stderr[-2000:])
@@ -423,9 +436,10 @@ def oracle_baseline_entry(o, full=None):
     v = o["nli"] / o["seconds"]
     e = {"value": v, "unit": UNIT, "cores": o["threads"], "kind": "oracle",
          "sample": (f"oracle Algorithm 4 (Jacobi-CG potential solve) on {o['sample']} (the same recipe at reduced "
-                    f"resolution: {o['n_phi']} potential unknowns, {o['n_mag']} magnetic nodes) from m0 at field "
-                    f"indices {o['fields']}, {o['nli']} NCG iterations, {o['evals']} evaluations, {o['mi']} "
-                    f"potential steps, {o['seconds']:.1f} s; assembly ({o['assembly_s']:.1f} s) excluded")}
+                    f"resolution: {o['n_phi']} potential unknowns, {o['n_mag']} magnetic nodes) from m0"
+                    + (f", after {o['warm_iter']} untimed warm-up iterations," if o.get("warm_iter") else "")
+                    + f" at field indices {o['fields']}, {o['nli']} NCG iterations, {o['evals']} evaluations, "
+                    f"{o['mi']} potential steps, {o['seconds']:.1f} s; assembly ({o['assembly_s']:.1f} s) excluded")}
     if full and o["nli"] and o["mi"]:
         n_phi_full, mi_per_it_full = full
         scale = (n_phi_full / o["n_phi"]) * (mi_per_it_full / (o["mi"] / o["nli"]))
@@ -546,6 +560,7 @@ def main():
     ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-first-field", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-iters", type=int, default=5, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-warm-iters", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-plan-leg", nargs=2, metavar=("KIND", "WORKLOAD"), help=argparse.SUPPRESS)
     ap.add_argument("--plan-legs", default="", help="oracle_plan mode: kind:workload legs to run (default all)")
     ap.add_argument("--record-traffic", nargs=3, metavar=("NCU_CSV", "JSON_LINE", "COMMAND"),
@@ -563,7 +578,8 @@ def main():
     if args.mode == "oracle_plan":
         return oracle_plan_mode(args)
     if args.oracle_leg:
-        print(json.dumps(oracle_sample(args.workload, args.oracle_first_field, args.oracle_iters)))
+        print(json.dumps(oracle_sample(args.workload, args.oracle_first_field, args.oracle_iters,
+                                       warm_iter=args.oracle_warm_iters)))
         return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -572,16 +588,18 @@ def main():
 
     if args.impl == "reference":
         # the oracle (no reference implementation exists: the reference is
-        # the paper's text), timed on the host cores for exactly K NCG
-        # iterations; one step = one NCG iteration (the metric's unit)
+        # the paper's text), timed on the host cores: W untimed NCG
+        # iterations, then exactly K timed ones; one step = one NCG
+        # iteration (the metric's unit)
         if rank != 0:
             return 0
         cores = os.cpu_count() or 1
-        o = oracle_leg(args.workload, W, K, cores)
+        o = oracle_leg(args.workload, W, K, cores, warm_iter=W)
         v = o["nli"] / o["seconds"]
         cb = oracle_baseline_entry(o)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": o["nli"], "warmup": 0, "ms_per_step": 1000.0 * o["seconds"] / max(o["nli"], 1),
+                "steps": o["nli"], "warmup": o["warm_iter"],
+                "ms_per_step": 1000.0 * o["seconds"] / max(o["nli"], 1),
                 "step": "one NCG iteration of the oracle", "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": dict(workload_desc(args.workload, workload(args.workload, sample=True)),
