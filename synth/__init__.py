@@ -9,10 +9,11 @@ method's code.
 from .mesh import Mesh, kuhn_lattice, cube_in_box, jitter_nodes, voronoi_regions, grain_patches
 from .workloads import (Workload, soft_cube, hard_cube, polycrystal_cube,
                         small_cube, random_unit_vectors, cone_axes, platelet,
-                        platelet_batch, graded_cube_in_box, large_polycrystal, sp3_cube)
+                        platelet_batch, graded_cube_in_box, large_polycrystal, sp3_cube,
+                        sphere_in_box)
 
 __all__ = ["Mesh", "kuhn_lattice", "cube_in_box", "jitter_nodes",
            "voronoi_regions", "grain_patches", "Workload", "soft_cube", "hard_cube",
            "polycrystal_cube", "small_cube", "random_unit_vectors",
            "cone_axes", "platelet", "platelet_batch",
-           "graded_cube_in_box", "large_polycrystal", "sp3_cube"]
+           "graded_cube_in_box", "large_polycrystal", "sp3_cube", "sphere_in_box"]

@@ -288,3 +288,23 @@ def platelet_batch(n=64, seed=4, lateral=(100e-9, 500e-9), thickness=5e-9, n_fie
         out.append(platelet(shape, a, b, thickness=thickness, h=h, seed=seed * 1000 + k,
                             n_fields=n_fields))
     return out
+
+
+def sphere_in_box(n_rad=8, h=1e-9, box_factor=6.0, ratio=1.15, Ms=8.0e5, A=1.3e-11):
+    """A sphere magnet of radius n_rad * h on a Kuhn lattice (the tets whose
+    centroid lies inside the sphere; a staircase surface) in a cubic air box
+    of box_factor x the radius per half-edge, uniform spacing h over the
+    sphere's bounding cube and graded by `ratio` per cell outside it; m0 =
+    +z, no anisotropy, zero field."""
+    R = n_rad * h
+    ax = _graded_axis(R, h, box_factor * R, ratio)
+    xyz, tets, _ = kuhn_lattice(ax, ax, ax)
+    c = xyz[tets].mean(axis=1)
+    inside = (np.einsum("ij,ij->i", c, c) < R * R).astype(np.int32)
+    nv = len(ax) - 1
+    mesh = Mesh(xyz=xyz, tets=tets, region=inside, shape=(nv + 1,) * 3, spacing=h,
+                meta={"radius": R, "box_factor": box_factor, "graded_ratio": ratio})
+    mats = _material_table([(0, 0, 0, 0, 0, 1), (Ms, A, 0.0, 0.0, 0.0, 1.0)])
+    m0 = np.tile([0.0, 0.0, 1.0], (mesh.n_nodes, 1))
+    return Workload(name=f"sphere_{n_rad}h", mesh=mesh, materials=mats, fields=np.zeros((1, 3)), m0=m0,
+                    meta={"radius": R, "h": h})

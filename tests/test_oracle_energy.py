@@ -112,3 +112,31 @@ def test_demag_factor_of_cube_tends_to_one_third():
     Linf = res[6.0] + (res[6.0] - res[3.0]) / (2.0 ** 3 - 1.0)
     assert Linf == pytest.approx(1.0 / 3.0, rel=0.15)
     assert Linf > res[6.0]
+
+
+def test_sphere_interior_field_is_uniform_one_third():
+    """A uniformly magnetised sphere has a uniform interior field H = -M/3,
+    i.e. the potential of K_phi phi = D m is phi = z/3 (reduced units,
+    lengths in nm) inside it.  On a staircase sphere of radius 6 h the
+    potential at the nodes within half the radius is fitted by a linear
+    function: it is linear to 0.1% of its range, its gradient points along
+    m (the x and y slopes vanish to 1e-3), and the slope along m, after
+    Richardson extrapolation of the grounded box's O(L^-3) truncation, is
+    1/3 within 1% (the staircase surface leaves 0.4%)."""
+    slopes = {}
+    for bf in (3.0, 6.0):
+        wl = synth.sphere_in_box(n_rad=6, h=1e-9, box_factor=bf, ratio=1.15)
+        P = fem.assemble_workload(wl)
+        phi, _ = energy.solve_potential(P, np.tile([0.0, 0.0, 1.0], (P.n_mag, 1)))
+        xyz = wl.mesh.xyz[P.free_nodes] * 1e9
+        sel = np.linalg.norm(xyz, axis=1) < 3.0
+        A = np.c_[xyz[sel], np.ones(sel.sum())]
+        coef, *_ = np.linalg.lstsq(A, phi[sel], rcond=None)
+        rms = np.sqrt(np.mean((A @ coef - phi[sel]) ** 2))
+        assert sel.sum() > 50
+        assert rms < 1e-3 * (2.0 * 3.0 * coef[2])              # 0.1% of the range of phi there
+        assert abs(coef[0]) < 1e-3 and abs(coef[1]) < 1e-3
+        slopes[bf] = coef[2]
+    assert slopes[3.0] < slopes[6.0] < 1.0 / 3.0
+    s_inf = slopes[6.0] + (slopes[6.0] - slopes[3.0]) / (2.0 ** 3 - 1.0)
+    assert s_inf == pytest.approx(1.0 / 3.0, rel=0.01)
