@@ -121,3 +121,42 @@ def test_jmax_zero_and_first_step_negative_curvature():
     y2, steps2 = precond.precond_solve(P, m, fake_grad, g2, jmax=5)
     assert steps2 == 1
     np.testing.assert_array_equal(y2, g2)
+
+
+def test_li3_stops_at_the_first_step_below_the_forcing_term():
+    """li3 (Sec. 3.1): the inner solve stops at the first step whose residual
+    |g - H y| falls below min(0.5, sqrt(|g|)) |g|.  The residuals are
+    recomputed here with the dense operator, independently of Algorithm 1's
+    recurrences: below the forcing term at the returned step, not below it
+    one step earlier (the same solve capped by li1 at one step less; before
+    the first step y = 0 and the residual is |g|).  Two gradient scales
+    take the two branches of the min: |g| ~ 240 (forcing 0.5) and
+    |g| ~ 2.4e-4 (forcing sqrt|g| ~ 0.015, 16 steps)."""
+    wl, P = _problem_no_demag()
+    rng = np.random.default_rng(3)
+    m = energy.normalize(np.tile([0.0, 0.0, 1.0], (P.n_mag, 1)) + 0.2 * rng.normal(size=(P.n_mag, 3)))
+    n = P.n_mag
+    h = P.units.field_int([0.0, 0.0, 8.0])
+    Hd = np.zeros((3 * n, 3 * n))
+    for scale, branch in ((1.0, "half"), (1e-6, "sqrt")):
+        grad = scale * energy.gradient(P, m, np.zeros(P.n_phi), h)
+        g = energy.project(m, grad)
+        for k in range(3 * n):
+            e = np.zeros(3 * n)
+            e[k] = 1
+            Hd[:, k] = precond.apply_H(P, m, grad, e.reshape(n, 3)).ravel()
+        ng = np.linalg.norm(g)
+        eta = min(0.5, np.sqrt(ng))
+        assert (eta == 0.5) == (branch == "half")
+        counts = {}
+        y, steps = precond.precond_solve(P, m, grad, g, jmax=2000, counts=counts)
+        assert 1 <= steps < 2000 and not counts.get("li2")
+        res = np.linalg.norm(g.ravel() - Hd @ y.ravel()) / ng
+        if steps > 1:
+            y1, s1 = precond.precond_solve(P, m, grad, g, jmax=steps - 1)
+            assert s1 == steps - 1
+            res1 = np.linalg.norm(g.ravel() - Hd @ y1.ravel()) / ng
+        else:
+            res1 = 1.0
+        assert res < eta <= res1, (branch, res, eta, res1)
+    assert steps >= 10
