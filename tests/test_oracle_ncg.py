@@ -237,3 +237,31 @@ def test_tolerance_schedule_keeps_the_minimum():
     assert r1.F == pytest.approx(r0.F, rel=1e-9)
     assert np.abs(r1.m - r0.m).max() < 1e-6
     assert r1.stats["mi"] < r0.stats["mi"]
+
+
+def test_stops_at_the_first_iteration_where_t1_t2_t3_hold():
+    """Sec. 3.1: Algorithm 4 stops once t1 (energy decrease below
+    tau_F (1 + |F|)), t2 (largest component step below sqrt(tau_F)
+    (1 + |m|_inf)) and t3 (largest projected-gradient component below
+    tau_F^(1/3) (1 + |F|)) hold together.  The three conditions are
+    evaluated here from the iterates themselves (the same run capped by
+    max_iter): all hold for the last iteration, not all for the one before."""
+    wl, P = _soft_problem()
+    m0 = energy.normalize(wl.m0[P.mag_nodes])
+    h = P.units.field_int([0.05, 0.0, 0.02])
+    tau = 1e-10
+    r = ncg.minimize(P, m0, h, ncg.Params(jmax=3, tau_F=tau))
+    n = r.stats["nli"]
+    assert r.status == "converged" and n >= 3
+    it = {k: ncg.minimize(P, m0, h, ncg.Params(jmax=3, tau_F=tau, max_iter=k)) for k in (n - 2, n - 1)}
+    it[n] = r
+
+    def rules(a, b):
+        t1 = a.F - b.F < tau * (1.0 + abs(b.F))
+        t2 = np.abs(a.m - b.m).max() < np.sqrt(tau) * (1.0 + np.abs(b.m).max())
+        t3 = np.abs(b.g).max() < tau ** (1.0 / 3.0) * (1.0 + abs(b.F))
+        return t1, t2, t3
+
+    assert all(rules(it[n - 1], it[n]))
+    assert not all(rules(it[n - 2], it[n - 1]))
+    assert it[n - 1].status == "max_iter"
