@@ -140,3 +140,23 @@ def test_sphere_interior_field_is_uniform_one_third():
     assert slopes[3.0] < slopes[6.0] < 1.0 / 3.0
     s_inf = slopes[6.0] + (slopes[6.0] - slopes[3.0]) / (2.0 ** 3 - 1.0)
     assert s_inf == pytest.approx(1.0 / 3.0, rel=0.01)
+
+
+def test_variational_demag_energy_error_is_quadratic():
+    """The magnetostatic energy is evaluated in the variational form
+    phi.b - 1/2 phi.K phi, whose value at phi* + e v (phi* the exact
+    potential) is the exact energy 1/2 phi*.b minus 1/2 e^2 v.K v: no term
+    linear in the potential error, so an inexact potential solve costs only
+    its square."""
+    wl, P = _problem()
+    m = energy.normalize(wl.m0[P.mag_nodes])
+    phi, _ = energy.solve_potential(P, m)
+    exact = 0.5 * float(phi @ energy.poisson_rhs(P, m))
+    e0 = energy.energy_terms(P, m, phi, np.zeros(3))["demag"]
+    assert e0 == pytest.approx(exact, rel=1e-12)
+    v = np.random.default_rng(8).normal(size=P.n_phi)
+    vKv = float(v @ (P.Kphi @ v))
+    for eps in (1e-2, 1e-3):
+        e = energy.energy_terms(P, m, phi + eps * v * np.abs(phi).max(), np.zeros(3))["demag"]
+        want = exact - 0.5 * (eps * np.abs(phi).max()) ** 2 * vKv
+        assert e == pytest.approx(want, rel=1e-9, abs=1e-12 * abs(exact))
