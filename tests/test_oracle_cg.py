@@ -1,7 +1,6 @@
 """Pins of Algorithm 1 (preconditioned linear CG) against dense linear
 algebra."""
 import numpy as np
-import pytest
 
 from oracle.linear_cg import alg1
 

@@ -2,7 +2,6 @@
 forms, invariants and brute force."""
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
 import synth
 from oracle import fem, energy

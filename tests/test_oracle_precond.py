@@ -1,7 +1,6 @@
 """Pins of the approximate-Hessian preconditioner (Eq. precond) and its
 truncated solve (Algorithm 1 with li1-li3)."""
 import numpy as np
-import pytest
 import scipy.sparse as sp
 
 import synth
