@@ -35,3 +35,19 @@ def test_create_fails_loudly_without_gpu():
         pytest.skip("library not built")
     with pytest.raises(MMError):
         Magnet(device=0)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/mmncg.h is a C header: it compiles as C99 with -pedantic, so
+    callers outside C++ and PyTorch can use the library."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "mmncg.h"\nint main(void) { mm_params p; mm_default_params(&p); return p.jmax; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use_header.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
