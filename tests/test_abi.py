@@ -51,3 +51,34 @@ def test_header_is_plain_c(tmp_path):
                         os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use_header.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_and_calls_host_entry_points(tmp_path):
+    """A C program links libmmncg.so and calls two entry points that need no
+    GPU: the default parameters of Algorithm 4 and the batch team split
+    (blocks in proportion to work, largest remainders, summing to the grid)."""
+    import shutil
+    import subprocess
+    from paper_1801_03690_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None or not os.path.exists(_lib.LIB_PATH):
+        pytest.skip("no C compiler or library not built")
+    src = tmp_path / "use_lib.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "mmncg.h"\n'
+        "int main(void) {\n"
+        "    mm_params p; int64_t work[3] = {100, 400, 900}; int32_t b[3];\n"
+        "    mm_default_params(&p);\n"
+        "    if (mm_batch_plan(3, work, 60, 1.0, b) != 0) return 1;\n"
+        '    printf("%d %g %d %d %d\\n", p.jmax, p.tau_F, b[0], b[1], b[2]);\n'
+        "    return 0;\n}\n")
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    exe = tmp_path / "use_lib"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir,
+                        "-lmmncg", f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    jmax, tau, *blocks = r.stdout.split()
+    assert int(jmax) == 4 and float(tau) == 1e-10
+    assert [int(x) for x in blocks] == [4, 17, 39]          # 60 x (1, 4, 9) / 14, largest remainders
